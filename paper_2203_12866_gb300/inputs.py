@@ -1,0 +1,87 @@
+"""Seeded synthetic initial states (host numpy arrays, FP64).
+
+This module only builds inputs; it contains none of the solver's arithmetic.
+Both the CUDA path and the CPU oracle receive the arrays it returns, so
+neither side draws random numbers of its own.
+
+State layout: float64 [2 species][4 components][nz][nv], species (nu, nubar),
+components (rho_ee, rho_xx, Re rho_ex, Im rho_ex), v fastest.
+
+Recipe of the collective-oscillation runs (Sec. 5 of arXiv:2203.12866):
+  * angular distributions g(v) proportional to exp(-(v-1)^2 / (2 sigma^2)), Sec. 5,
+    normalised on the grid (sum_j w_j g_j = 1 with midpoint bins, w_j = 2/nv);
+  * neutrino state S_ee = g_nu, S_xx = 0; antineutrino state carries alpha:
+    Sbar_ee = alpha g_nubar, Sbar_xx = 0;
+  * off-diagonal seed S_ex = Sbar_ex = eps0 exp(i phi(z)), phi(z_i) uniform
+    on [0, 2 pi) drawn per cell by splitmix64(seed XOR i); u = (x >> 11) 2^-53.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+_M64 = (1 << 64) - 1
+
+
+def splitmix64(x: np.ndarray) -> np.ndarray:
+    """splitmix64 finaliser (Steele, Lea, Flood 2014) on uint64 arrays."""
+    x = (x.astype(np.uint64) + np.uint64(0x9E3779B97F4A7C15)) & np.uint64(_M64)
+    x = (x ^ (x >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+    x = (x ^ (x >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return x ^ (x >> np.uint64(31))
+
+
+def uniform01(n: int, seed: int) -> np.ndarray:
+    """n doubles in [0, 1): (splitmix64(seed ^ i) >> 11) * 2^-53."""
+    with np.errstate(over="ignore"):
+        i = np.arange(n, dtype=np.uint64) ^ np.uint64(seed & _M64)
+        x = splitmix64(i)
+    return (x >> np.uint64(11)).astype(np.float64) * (2.0 ** -53)
+
+
+def beam_velocities(nv: int) -> np.ndarray:
+    """Bin midpoints on [-1, 1] (where the angular distributions are sampled)."""
+    return -1.0 + (np.arange(nv) + 0.5) * (2.0 / nv)
+
+
+def angular_gaussian(nv: int, sigma: float) -> np.ndarray:
+    """g(v) ~ exp(-(v-1)^2/(2 sigma^2)) sampled at bin midpoints, sum(w g) = 1."""
+    v = beam_velocities(nv)
+    g = np.exp(-((v - 1.0) ** 2) / (2.0 * sigma * sigma))
+    return g / (g.sum() * (2.0 / nv))
+
+
+def collective_state(nz: int, nv: int, *, alpha=0.9, sigma_nu=0.6, sigma_nubar=0.5,
+                     eps0=1e-6, seed=12866) -> np.ndarray:
+    """Initial state of the collective runs with a random-phase seed."""
+    g = angular_gaussian(nv, sigma_nu)
+    gb = angular_gaussian(nv, sigma_nubar)
+    phi = 2.0 * np.pi * uniform01(nz, seed)
+    s = np.zeros((2, 4, nz, nv))
+    s[0, 0] = g[None, :]
+    s[1, 0] = alpha * gb[None, :]
+    for sp in range(2):
+        s[sp, 2] = (eps0 * np.cos(phi))[:, None]
+        s[sp, 3] = (eps0 * np.sin(phi))[:, None]
+    return s
+
+
+def random_state(nz: int, nv: int, seed: int, scale=1.0, offdiag=0.1) -> np.ndarray:
+    """Generic seeded state for parity tests: diagonal in [0.5, 1.5) * scale,
+    off-diagonal uniform in [-offdiag, offdiag) * scale."""
+    u = uniform01(8 * nz * nv, seed).reshape(2, 4, nz, nv)
+    s = np.empty_like(u)
+    s[:, 0:2] = (0.5 + u[:, 0:2]) * scale
+    s[:, 2:4] = (2.0 * u[:, 2:4] - 1.0) * offdiag * scale
+    return s
+
+
+def single_mode_state(nz: int, nv: int, k_index: int, *, alpha=0.9, sigma_nu=0.6,
+                      sigma_nubar=0.5, eps0=1e-8) -> np.ndarray:
+    """Collective state seeded with one Fourier mode exp(i k z), k = 2 pi k_index / L,
+    on the neutrino off-diagonal only."""
+    s = collective_state(nz, nv, alpha=alpha, sigma_nu=sigma_nu, sigma_nubar=sigma_nubar,
+                         eps0=0.0)
+    ph = 2.0 * np.pi * k_index * np.arange(nz) / nz
+    s[0, 2] = (eps0 * np.cos(ph))[:, None]
+    s[0, 3] = (eps0 * np.sin(ph))[:, None]
+    return s
