@@ -1,0 +1,437 @@
+#!/usr/bin/env python
+"""Benchmark of the COSEnu RK4-stage engine on GB300.
+
+Workload (the roofline run): nz = 2^20 z cells, nv = 256 v bins, both species,
+4 real components each; z in [-25600, 25600) (dz = 0.048828125), dt = 0.4 dz,
+mu = 10, omega = 0, alpha = 0.9, sigma_nu = 0.6, sigma_nubar = 0.5, random-phase
+off-diagonal seed 1e-6 (splitmix64, seed 12866).  A step is one full RK4 step
+(four fused stage kernels) over the whole grid.  Metric: cell-updates/s, a cell
+being one (z, v, species) triple advanced by one RK4 step.
+
+Default arm: the CUDA library through its C ABI, mixed precision, FD4 + KO.
+The line also carries the other three (scheme, precision) variants, the
+roofline of the dominant stage kernel, an end-to-end figure through the C ABI
+with host buffers, the oracle timed on the host cores, and clocks sampled
+during the timed region.
+
+--impl reference: the FP64 CPU oracle on a z-slab sample of the same workload.
+
+Several GPUs (torchrun): independent replicas, one per rank (the workload is
+one periodic grid per GPU; no data crosses GPUs), timed with a barrier and the
+maximum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NZ, NV = 1 << 20, 256
+DZ = 3200.0 / 65536.0
+L = NZ * DZ
+MU, ALPHA, SIG_NU, SIG_NUBAR, EPS0, SEED = 10.0, 0.9, 0.6, 0.5, 1e-6, 12866
+WORKLOAD = ("roofline run: nz=2^20, nv=256, z in [-25600,25600), dt=0.4 dz, mu=10, omega=0, "
+            "alpha=0.9, sigma=(0.6,0.5), random-phase seed 1e-6")
+
+# Algorithmic HBM bytes per real component per launch of each RK4 stage
+# (state y in double; stage increments in double (fp64) or float (mixed)):
+#   stage 1: read y, write d1; stage 2: read y, d1, write d2; stage 3: read y, d2,
+#   write d3; stage 4: read y, d3, d1, d2, write y.
+STAGE_BYTES = {"fp64": (16, 24, 24, 40), "mixed": (12, 16, 16, 28)}
+# Algorithmic FP64 flops per cell (4 reals) per launch of the fp64 stages
+# (moments, Hamiltonian, commutator, stencil, RK axpy; FMA = 2 flops).
+FP64_FLOPS_PER_CELL = {"fdko": (98, 106, 106, 138), "weno7": (482, 490, 490, 522)}
+SCHEMES = {"fdko": 0, "weno7": 1}
+PRECS = {"fp64": 0, "mixed": 1}
+# 152 SMs x 2 FP64 FMA lanes per clock x 2 flops x 2.07 GHz (nominal 1.25 TFLOP/s)
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ ncu traffic
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("stage_kernel.cuh", "cosenu_device.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2203_12866_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(scheme, prec, stage):
+    """DRAM bytes per launch of the stage kernel from the committed ncu summary,
+    scaled to this workload; None when absent or taken on different source."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    rec = d.get("kernels", {}).get(f"{scheme}_{prec}_stage{stage}")
+    if not rec:
+        return None
+    return rec["dram_bytes_per_launch"] * (8 * NZ * NV) / rec["reals_per_launch"]
+
+
+# ------------------------------------------------------------------ distributed
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        if args.impl == "reference":
+            dist.init_process_group("gloo")
+        else:
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl")
+    return world, rank, local
+
+
+def dist_max(x, world, device=None):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world, device=None):
+    if world > 1:
+        import torch.distributed as dist
+        if device is not None:
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+# ------------------------------------------------------------------ oracle arm
+
+
+def oracle_rate(rows, steps, scheme="fdko"):
+    """Cell-updates/s of the FP64 oracle on a periodic z-slab of `rows` rows of the
+    workload (same dz, nv, parameters); returns (rate, seconds, threads)."""
+    import oracle
+    from paper_2203_12866_gb300 import inputs
+    oracle.build()
+    u0 = inputs.collective_rows(range(rows), NV, alpha=ALPHA, sigma_nu=SIG_NU,
+                                sigma_nubar=SIG_NUBAR, eps0=EPS0, seed=SEED)
+    p = oracle.params(rows, NV, rows * DZ, SCHEMES[scheme], mu=MU, cfl=0.4)
+    t0 = time.perf_counter()
+    oracle.step(p, u0, steps)
+    dt = time.perf_counter() - t0
+    return 2 * rows * NV * steps / dt, dt, oracle.num_threads()
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import oracle
+    rows = args.cpu_rows
+    oracle_rate(min(rows, 256), 1)  # build, page in
+    for _ in range(args.warmup):
+        oracle_rate(rows, 1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle_rate(rows, 1)
+    sec = time.perf_counter() - t0
+    value = 2 * rows * NV * args.steps / sec
+    sample = f"z-slab of {rows} rows x nv=256 x 2 species (periodic, same dz and parameters), FD+KO"
+    line = {
+        "impl": "reference", "metric": "cell-updates/s (z*v*species per RK4 step)",
+        "value": value, "unit": "cell-updates/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * sec / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "scheme": "FD+KO", "precision": "fp64 (oracle)",
+                   "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "cell-updates/s", "cores": oracle.num_threads(),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "cell-updates/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+
+
+def stage_roofline(stage_ms, stage_n, prec, scheme, hbm_peak):
+    out = []
+    reals = 8 * NZ * NV
+    for s in range(4):
+        if stage_n[s] == 0:
+            continue
+        avg_ms = stage_ms[s] / stage_n[s]
+        byts = STAGE_BYTES[prec][s] * reals
+        gbs = byts / (avg_ms * 1e-3) / 1e9
+        rec = {"stage": s + 1, "avg_ms": avg_ms, "alg_bytes": byts, "GB/s": gbs,
+               "hbm_frac": gbs / hbm_peak, "total_ms": stage_ms[s]}
+        if prec == "fp64":
+            fl = FP64_FLOPS_PER_CELL[scheme][s] * 2 * NZ * NV
+            rec["fp64_tflops"] = fl / (avg_ms * 1e-3) / 1e12
+            rec["fp64_alu_frac"] = rec["fp64_tflops"] / FP64_PEAK_TFLOPS
+        out.append(rec)
+    return out
+
+
+def run_variant(b, scheme, prec, steps, warmup, device, stream, state_dev):
+    import torch
+    h = b.cosenu_create(NZ, NV, L, SCHEMES[scheme], PRECS[prec])
+    try:
+        b.cosenu_set_stream(h, stream.cuda_stream)
+        b.cosenu_set_params(h, mu=MU)
+        b.cosenu_set_state_device(h, state_dev.data_ptr(), state_dev.numel())
+        b.cosenu_step(h, warmup)
+        b.cosenu_sync(h)
+        torch.cuda.synchronize(device)
+        b.cosenu_set_stage_timing(h, True)
+        b.cosenu_stage_times(h)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.cosenu_step(h, steps)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        sms, sn = b.cosenu_stage_times(h)
+        b.cosenu_sync(h)
+        return ms, sms, sn
+    finally:
+        b.cosenu_destroy(h)
+
+
+def run_ours(args, world, rank, local):
+    import torch
+
+    from paper_2203_12866_gb300 import binding as b
+    from paper_2203_12866_gb300 import inputs
+
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    b.load()
+    hbm_peak, peak_kind = peaks()
+    stream = torch.cuda.Stream(device)
+    scheme, prec = args.scheme, args.precision
+    cells = 2 * NZ * NV
+
+    # ---- main timed region: inputs resident in HBM
+    h = b.cosenu_create(NZ, NV, L, SCHEMES[scheme], PRECS[prec])
+    b.cosenu_set_stream(h, stream.cuda_stream)
+    b.cosenu_set_params(h, mu=MU)
+    with torch.cuda.stream(stream):
+        state = inputs.collective_state_device(NZ, NV, device, alpha=ALPHA, sigma_nu=SIG_NU,
+                                               sigma_nubar=SIG_NUBAR, eps0=EPS0, seed=SEED)
+    stream.synchronize()
+    b.cosenu_set_state_device(h, state.data_ptr(), state.numel())
+    b.cosenu_step(h, args.warmup)
+    b.cosenu_sync(h)
+    b.cosenu_set_stage_timing(h, True)
+    b.cosenu_stage_times(h)
+    torch.cuda.synchronize(device)
+    barrier(world, device)
+    torch.cuda.synchronize(device)
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = b.cosenu_kernel_launches()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    b.cosenu_step(h, args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize(device)
+    launches = b.cosenu_kernel_launches() - l0
+    barrier(world, device)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    stage_ms, stage_n = b.cosenu_stage_times(h)
+    b.cosenu_sync(h)
+    cons = b.cosenu_conserved(h)
+    ms_max = dist_max(ms, world, device)
+    ms_step = ms_max / args.steps
+    value = world * cells / (ms_step * 1e-3)
+    stages = stage_roofline(stage_ms, stage_n, prec, scheme, hbm_peak)
+    dom = max(stages, key=lambda r: r["total_ms"])
+    traffic = ncu_traffic(scheme, prec, dom["stage"])
+    roofline = {"bound": "hbm", "achieved": dom["GB/s"], "peak": hbm_peak, "unit": "GB/s",
+                "frac": dom["hbm_frac"], "traffic": traffic,
+                "kernel": f"rk4_stage_kernel<{scheme},{prec},stage {dom['stage']}>",
+                "peak_kind": f"{peak_kind} (copy)", "stages": stages,
+                "step_frac": (sum(STAGE_BYTES[prec]) * 8 * NZ * NV / (ms_step * 1e-3) / 1e9)
+                / hbm_peak}
+
+    # ---- end to end through the C ABI with host buffers: each step copies the
+    # state in from pinned host memory, steps, and reads the new state back
+    e2e = None
+    if args.e2e_steps > 0:
+        n = 8 * NZ * NV
+        host = torch.empty(n, dtype=torch.float64, pin_memory=True)
+        hp = host.numpy()
+        b.cosenu_get_state(h, hp)
+        b.cosenu_set_state(h, hp)  # warm the path
+        b.cosenu_step(h, 1)
+        b.cosenu_get_state(h, hp)
+        barrier(world, device)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            b.cosenu_set_state(h, hp)
+            b.cosenu_step(h, 1)
+            b.cosenu_get_state(h, hp)
+        sec = dist_max(time.perf_counter() - t0, world, device)
+        e2e = {"value": world * cells * args.e2e_steps / sec, "unit": "cell-updates/s",
+               "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8,
+               "steps": args.e2e_steps, "api": "cosenu_set_state + cosenu_step(1) + cosenu_get_state"}
+        del host, hp
+    b.cosenu_destroy(h)
+
+    # ---- the other (scheme, precision) variants on the same input
+    variants = {}
+    if args.variants:
+        for sc in ("fdko", "weno7"):
+            for pr in ("mixed", "fp64"):
+                if (sc, pr) == (scheme, prec):
+                    continue
+                k = args.variant_steps if pr == "mixed" else max(1, args.variant_steps // 4)
+                vms, vsm, vsn = run_variant(b, sc, pr, k, 1, device, stream, state)
+                vst = stage_roofline(vsm, vsn, pr, sc, hbm_peak)
+                rec = {"value": cells / (vms / k * 1e-3), "ms_per_step": vms / k, "steps": k,
+                       "step_hbm_frac": (sum(STAGE_BYTES[pr]) * 8 * NZ * NV /
+                                         (vms / k * 1e-3) / 1e9) / hbm_peak,
+                       "stages": vst}
+                if pr == "fp64":
+                    fl = sum(FP64_FLOPS_PER_CELL[sc]) * cells
+                    rec["bound"] = "alu"
+                    rec["fp64_tflops"] = fl / (vms / k * 1e-3) / 1e12
+                    rec["fp64_alu_frac"] = rec["fp64_tflops"] / FP64_PEAK_TFLOPS
+                variants[f"{sc}_{pr}"] = rec
+    del state
+    torch.cuda.empty_cache()
+
+    # ---- oracle on the host cores (rank 0, one GPU only)
+    cpu = None
+    if args.cpu_baseline and world == 1 and rank == 0:
+        rate, sec, thr = oracle_rate(args.cpu_rows, args.cpu_steps, scheme)
+        cpu = {"value": rate, "unit": "cell-updates/s", "cores": thr, "kind": "oracle",
+               "sample": f"z-slab of {args.cpu_rows} rows x nv=256 x 2 species, {args.cpu_steps} "
+                         f"RK4 steps ({sec:.1f} s), FP64 {scheme}, same dz and parameters"}
+
+    if rank == 0:
+        line = {
+            "metric": "cell-updates/s (z*v*species per RK4 step)", "value": value,
+            "unit": "cell-updates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if prec == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "scheme": "FD+KO" if scheme == "fdko" else "WENO7",
+                       "precision": prec, "nz": NZ, "nv": NV, "cells_per_step": cells,
+                       "l2": "inputs larger than L2 (state 17.2 GB >> 129 MB)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk, "variants": variants,
+            "conserved_after": {"tr_nu": cons["tr_nu"], "M": list(cons["M"]),
+                                "dP_max": cons["dP_max"]},
+        }
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scheme", default="fdko", choices=["fdko", "weno7"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-variants", dest="variants", action="store_false")
+    ap.add_argument("--variant-steps", type=int, default=8)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--cpu-rows", type=int, default=8192)
+    ap.add_argument("--cpu-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,188 @@
+/*
+ * cosenu.h -- C ABI of the GB300 COSEnu engine (libcosenu.so).
+ *
+ * The engine advances the two-flavour neutrino quantum kinetic equations
+ *     (d_t + v d_z) rho    = -i [H,    rho]
+ *     (d_t + v d_z) rhobar = -i [Hbar, rhobar]
+ * (arXiv:2203.12866, Sec. 2, Eq. (eom)) on a periodic z grid times N_v
+ * velocity bins, with the Hamiltonian of Eq. (ham), 4th-order central
+ * differences plus Kreiss-Oliger dissipation (Sec. 3.1) or the finite-volume
+ * WENO7 flux (Sec. 3.2, Appendix A), and classic RK4 in time.
+ *
+ * Grid.  z in [-L/2, L/2), nz cells of width dz = L/nz, periodic (Sec. 4).
+ * v bins: v_j = -1 + (j + 1/2) dv, dv = 2/nv, integrals over v are Riemann
+ * sums with weight dv (Sec. 3).
+ *
+ * State layout (host and device): double [2][4][nz][nv]
+ *   species (0 = nu, 1 = nubar) x component (0 = rho_ee, 1 = rho_xx,
+ *   2 = Re rho_ex, 3 = Im rho_ex) x z x v, v fastest.
+ * The stored neutrino state is g_nu(v) rho (Sec. 5); the stored antineutrino
+ * state already carries the asymmetry factor: alpha g_nubar(v) rhobar.  The
+ * Hamiltonian therefore uses the stored antineutrino state where Eq. (ham)
+ * has alpha rhobar.
+ *
+ * Conventions.
+ *   - Return codes: 0 on success, a negative COSENU_E* code on failure.  No
+ *     C++ exception crosses this boundary.  cosenu_last_error() describes
+ *     the most recent failure (per handle; thread-local for NULL handles).
+ *   - A handle is not thread-safe; distinct handles are independent.
+ *   - cosenu_step() only enqueues work on the handle's stream and returns;
+ *     cosenu_get_state(), cosenu_moments(), cosenu_conserved() and
+ *     cosenu_sync() wait for it.
+ *   - Host pointers are read or written only during the call; the caller
+ *     keeps ownership.  Device memory is owned by the library unless the
+ *     handle was made by cosenu_create_external().
+ *   - Requirements: nz >= 1; 4 <= nv <= 256 and nv a multiple of 4
+ *     (rows are moved by 16-byte bulk copies).  Violations give COSENU_EINVAL.
+ */
+#ifndef COSENU_H
+#define COSENU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define COSENU_VERSION 1
+
+/* Spatial scheme: Sec. 3.1 (FD4 + Kreiss-Oliger r = 2) or Sec. 3.2 (FV WENO7). */
+enum { COSENU_FDKO = 0, COSENU_WENO7 = 1 };
+
+/* Arithmetic.  COSENU_FP64: every operation in double.  COSENU_MIXED: the
+ * state y and its RK4 update y += increment stay in double, the per-z
+ * velocity moments that form H_nunu are kept as double running sums, and the
+ * stencil / WENO / commutator arithmetic and the stage increments are float. */
+enum { COSENU_FP64 = 0, COSENU_MIXED = 1 };
+
+/* Error codes. */
+enum {
+  COSENU_OK = 0,
+  COSENU_EINVAL = -1,      /* bad argument or unsupported size */
+  COSENU_ENOMEM = -2,      /* device or host allocation failed */
+  COSENU_ECUDA = -3,       /* a CUDA runtime call failed */
+  COSENU_ENONFINITE = -4,  /* a non-finite value appeared in the state */
+  COSENU_ETIMEOUT = -5     /* a bounded device-side wait gave up */
+};
+
+/* Physical and numerical parameters (Sec. 2 and 3).
+ *   mu       strength of H_nunu, Eq. (ham)                         default 1
+ *   omega    vacuum oscillation frequency omega_vac                default 0
+ *   theta    vacuum mixing angle theta_vac (radians)               default 0
+ *   lambda   constant matter potential: +diag(lambda,0) for nu,
+ *            -diag(lambda,0) for nubar (0 in the paper)          default 0
+ *   ko_eps   Kreiss-Oliger strength eps_ko (Sec. 3.1, r = 2)       default 0.1
+ *   weno_eps epsilon of the WENO weights, Eq. (weight)             default 1e-6
+ *   dt       time step                            default 0.4 * dz (C_CFL 0.4) */
+typedef struct {
+  double mu, omega, theta, lambda, ko_eps, weno_eps, dt;
+} cosenu_params;
+
+/* Diagnostics (Sec. 2: P0, |P|; Sec. 5: M_0, delta P).  With
+ * P(d) = (2 Re d_ex, -2 Im d_ex, d_ee - d_xx) for a 2x2 matrix d:
+ *   tr_nu, tr_nubar  sum_{z,v} dv dz (rho_ee + rho_xx) of each species
+ *   M[3]             sum_{z,v} dv dz P(S - Sbar^*)  (the lepton-number vector)
+ *   M_vac            sin(2 theta) M[0] - cos(2 theta) M[2]
+ *   dP_max           max over cells and species of | |P| / P0 - 1 |
+ *   dP_mean          sum |P|/P0 - 1| P0 over nu cells / sum P0 over nu cells
+ *   step             RK4 steps taken since the last cosenu_set_state. */
+typedef struct {
+  double tr_nu, tr_nubar;
+  double M[3];
+  double M_vac;
+  double dP_max, dP_mean;
+  int64_t step;
+} cosenu_conserved_t;
+
+typedef struct cosenu_s* cosenu_t;
+
+/* Create a solver for an nz x nv grid on [-L/2, L/2) with the given scheme
+ * and precision; allocates all device memory (see cosenu_workspace_bytes).
+ * The state starts at zero and the parameters at their defaults.
+ * Returns NULL on failure; cosenu_last_error(NULL) gives the reason. */
+cosenu_t cosenu_create(int64_t nz, int32_t nv, double L, int scheme, int precision);
+
+/* Bytes of device memory one solver needs (state, RK4 stage buffers, moment
+ * sums, reduction scratch).  0 for invalid sizes. */
+size_t cosenu_workspace_bytes(int64_t nz, int32_t nv, int scheme, int precision);
+
+/* Like cosenu_create, but the solver lives in caller-owned device memory
+ * `workspace` of at least cosenu_workspace_bytes() bytes, 256-byte aligned,
+ * which must stay valid until cosenu_destroy.  Nothing is allocated on the
+ * device. */
+cosenu_t cosenu_create_external(int64_t nz, int32_t nv, double L, int scheme, int precision,
+                                void* workspace, size_t workspace_bytes);
+
+/* Release the handle and the device memory it allocated.  NULL is a no-op. */
+void cosenu_destroy(cosenu_t h);
+
+/* Set / read the parameters.  dt <= 0 selects the default 0.4 * dz. */
+int cosenu_set_params(cosenu_t h, const cosenu_params* p);
+int cosenu_get_params(cosenu_t h, cosenu_params* p);
+
+/* Use the given cudaStream_t (NULL = the legacy default stream) for all
+ * later work of this handle. */
+int cosenu_set_stream(cosenu_t h, void* stream);
+
+/* Copy a host state (n = 8 nz nv doubles, layout above) into the solver and
+ * reset the step counter.  Synchronous with respect to the host buffer. */
+int cosenu_set_state(cosenu_t h, const double* host, size_t n);
+
+/* Same from a device buffer of n doubles (stream-ordered, asynchronous). */
+int cosenu_set_state_device(cosenu_t h, const double* dev, size_t n);
+
+/* Copy the current state to a host buffer of n = 8 nz nv doubles (waits). */
+int cosenu_get_state(cosenu_t h, double* host, size_t n);
+
+/* Copy rows z0 .. z0+nrows-1 (0 <= z0, z0 + nrows <= nz) of every species and
+ * component to host: out[2][4][nrows][nv] doubles (waits).  For inspecting
+ * large grids without moving the whole state. */
+int cosenu_get_rows(cosenu_t h, int64_t z0, int64_t nrows, double* host);
+
+/* Device pointer of the current state (layout above); valid until the next
+ * cosenu_step / cosenu_set_state call. */
+const double* cosenu_state_device(cosenu_t h);
+
+/* Enqueue nsteps RK4 steps (4 fused stage kernels each) on the handle's
+ * stream.  nsteps = 0 is a no-op. */
+int cosenu_step(cosenu_t h, int64_t nsteps);
+
+/* Wait for the handle's stream; report COSENU_ENONFINITE if a non-finite
+ * value was written to the state, COSENU_ETIMEOUT if a device-side wait gave
+ * up.  The device error flags are cleared after they are reported. */
+int cosenu_sync(cosenu_t h);
+
+/* z-averaged state zavg[2][4][nv] and per-z velocity moments of S - Sbar^*
+ * vmom[nz][6] = (D3_0, D3_1, Dr_0, Dr_1, Di_0, Di_1) with
+ *   D3_n = sum_j dv v_j^n [(S_ee - S_xx) - (Sbar_ee - Sbar_xx)],
+ *   Dr_n = sum_j dv v_j^n (Re S_ex - Re Sbar_ex),
+ *   Di_n = sum_j dv v_j^n (Im S_ex + Im Sbar_ex)   (Eq. (ham)).
+ * Either output may be NULL.  Host buffers; waits. */
+int cosenu_moments(cosenu_t h, double* zavg, double* vmom);
+
+/* Diagnostics of the current state (waits). */
+int cosenu_conserved(cosenu_t h, cosenu_conserved_t* out);
+
+/* Stage timing.  With on != 0, every stage launch of later cosenu_step calls is
+ * bracketed by CUDA events on the handle's stream (and steps are launched
+ * directly rather than replayed from a graph).  cosenu_stage_times waits for
+ * the stream and returns, per RK4 stage s = 1..4, the summed device time in
+ * milliseconds ms[s-1] and the number of timed launches n[s-1] since the last
+ * call (either pointer may be NULL), then clears the sums. */
+int cosenu_set_stage_timing(cosenu_t h, int on);
+int cosenu_stage_times(cosenu_t h, double* ms, int64_t* n);
+
+/* Steps taken since the last cosenu_set_state. */
+int64_t cosenu_steps_taken(cosenu_t h);
+
+/* Description of the last error of h (of this thread for h = NULL). */
+const char* cosenu_last_error(cosenu_t h);
+
+/* Kernel launches the library has issued in this process (all handles). */
+uint64_t cosenu_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* COSENU_H */

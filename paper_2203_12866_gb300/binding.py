@@ -1,0 +1,278 @@
+"""Thin ctypes binding of libcosenu.so (include/cosenu.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  The functions keep the C names; ``Solver`` is a small convenience
+owner of one handle.  If the library is missing, loading raises -- there is no
+fallback of any kind.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libcosenu.so")
+
+COSENU_FDKO, COSENU_WENO7 = 0, 1
+COSENU_FP64, COSENU_MIXED = 0, 1
+COSENU_OK, COSENU_EINVAL, COSENU_ENOMEM, COSENU_ECUDA, COSENU_ENONFINITE, COSENU_ETIMEOUT = (
+    0, -1, -2, -3, -4, -5)
+
+# Every entry point include/cosenu.h declares.
+EXPORTS = (
+    "cosenu_create", "cosenu_workspace_bytes", "cosenu_create_external", "cosenu_destroy",
+    "cosenu_set_params", "cosenu_get_params", "cosenu_set_stream", "cosenu_set_state",
+    "cosenu_set_state_device", "cosenu_get_state", "cosenu_get_rows", "cosenu_state_device",
+    "cosenu_step",
+    "cosenu_sync", "cosenu_moments", "cosenu_conserved", "cosenu_set_stage_timing",
+    "cosenu_stage_times", "cosenu_steps_taken",
+    "cosenu_last_error", "cosenu_kernel_launches",
+)
+
+
+class cosenu_params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in
+                ("mu", "omega", "theta", "lambda_", "ko_eps", "weno_eps", "dt")]
+
+
+class cosenu_conserved_t(ctypes.Structure):
+    _fields_ = [("tr_nu", ctypes.c_double), ("tr_nubar", ctypes.c_double),
+                ("M", ctypes.c_double * 3), ("M_vac", ctypes.c_double),
+                ("dP_max", ctypes.c_double), ("dP_mean", ctypes.c_double),
+                ("step", ctypes.c_int64)]
+
+
+class CosenuError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"cosenu error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libcosenu.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with paper_2203_12866_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    vp, dp = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double)
+    i64, i32, sz = ctypes.c_int64, ctypes.c_int32, ctypes.c_size_t
+    sig = {
+        "cosenu_create": (vp, [i64, i32, ctypes.c_double, ctypes.c_int, ctypes.c_int]),
+        "cosenu_workspace_bytes": (sz, [i64, i32, ctypes.c_int, ctypes.c_int]),
+        "cosenu_create_external": (vp, [i64, i32, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                                        vp, sz]),
+        "cosenu_destroy": (None, [vp]),
+        "cosenu_set_params": (ctypes.c_int, [vp, ctypes.POINTER(cosenu_params)]),
+        "cosenu_get_params": (ctypes.c_int, [vp, ctypes.POINTER(cosenu_params)]),
+        "cosenu_set_stream": (ctypes.c_int, [vp, vp]),
+        "cosenu_set_state": (ctypes.c_int, [vp, dp, sz]),
+        "cosenu_set_state_device": (ctypes.c_int, [vp, vp, sz]),
+        "cosenu_get_state": (ctypes.c_int, [vp, dp, sz]),
+        "cosenu_get_rows": (ctypes.c_int, [vp, i64, i64, dp]),
+        "cosenu_state_device": (vp, [vp]),
+        "cosenu_step": (ctypes.c_int, [vp, i64]),
+        "cosenu_sync": (ctypes.c_int, [vp]),
+        "cosenu_moments": (ctypes.c_int, [vp, dp, dp]),
+        "cosenu_conserved": (ctypes.c_int, [vp, ctypes.POINTER(cosenu_conserved_t)]),
+        "cosenu_set_stage_timing": (ctypes.c_int, [vp, ctypes.c_int]),
+        "cosenu_stage_times": (ctypes.c_int, [vp, dp, ctypes.POINTER(i64)]),
+        "cosenu_steps_taken": (i64, [vp]),
+        "cosenu_last_error": (ctypes.c_char_p, [vp]),
+        "cosenu_kernel_launches": (ctypes.c_uint64, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _dptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _check(h, rc):
+    if rc != COSENU_OK:
+        raise CosenuError(rc, load().cosenu_last_error(h).decode())
+    return rc
+
+
+# ---------------------------------------------------------------- C-named wrappers
+
+def cosenu_create(nz, nv, L, scheme=COSENU_FDKO, precision=COSENU_FP64):
+    lib = load()
+    h = lib.cosenu_create(int(nz), int(nv), float(L), int(scheme), int(precision))
+    if not h:
+        raise CosenuError(COSENU_EINVAL, lib.cosenu_last_error(None).decode())
+    return h
+
+
+def cosenu_workspace_bytes(nz, nv, scheme=COSENU_FDKO, precision=COSENU_FP64):
+    return int(load().cosenu_workspace_bytes(int(nz), int(nv), int(scheme), int(precision)))
+
+
+def cosenu_create_external(nz, nv, L, scheme, precision, workspace_ptr, workspace_bytes):
+    lib = load()
+    h = lib.cosenu_create_external(int(nz), int(nv), float(L), int(scheme), int(precision),
+                                   ctypes.c_void_p(int(workspace_ptr)), int(workspace_bytes))
+    if not h:
+        raise CosenuError(COSENU_EINVAL, lib.cosenu_last_error(None).decode())
+    return h
+
+
+def cosenu_destroy(h):
+    load().cosenu_destroy(h)
+
+
+def cosenu_set_params(h, **kw):
+    p = cosenu_get_params(h)
+    for k, v in kw.items():
+        setattr(p, "lambda_" if k in ("lambda", "lam") else k, float(v))
+    return _check(h, load().cosenu_set_params(h, ctypes.byref(p)))
+
+
+def cosenu_get_params(h):
+    p = cosenu_params()
+    _check(h, load().cosenu_get_params(h, ctypes.byref(p)))
+    return p
+
+
+def cosenu_set_stream(h, stream_handle):
+    return _check(h, load().cosenu_set_stream(h, ctypes.c_void_p(int(stream_handle or 0))))
+
+
+def cosenu_set_state(h, host):
+    a = np.ascontiguousarray(host, dtype=np.float64)
+    return _check(h, load().cosenu_set_state(h, _dptr(a), a.size))
+
+
+def cosenu_set_state_device(h, dev_ptr, n):
+    return _check(h, load().cosenu_set_state_device(h, ctypes.c_void_p(int(dev_ptr)), int(n)))
+
+
+def cosenu_get_state(h, out):
+    assert out.dtype == np.float64 and out.flags["C_CONTIGUOUS"]
+    return _check(h, load().cosenu_get_state(h, _dptr(out), out.size))
+
+
+def cosenu_get_rows(h, z0, nrows, out):
+    assert out.dtype == np.float64 and out.flags["C_CONTIGUOUS"]
+    return _check(h, load().cosenu_get_rows(h, int(z0), int(nrows), _dptr(out)))
+
+
+def cosenu_state_device(h):
+    return int(load().cosenu_state_device(h) or 0)
+
+
+def cosenu_step(h, nsteps=1):
+    return _check(h, load().cosenu_step(h, int(nsteps)))
+
+
+def cosenu_sync(h):
+    return _check(h, load().cosenu_sync(h))
+
+
+def cosenu_moments(h, zavg=None, vmom=None):
+    return _check(h, load().cosenu_moments(h, _dptr(zavg), _dptr(vmom)))
+
+
+def cosenu_conserved(h):
+    c = cosenu_conserved_t()
+    _check(h, load().cosenu_conserved(h, ctypes.byref(c)))
+    return {"tr_nu": c.tr_nu, "tr_nubar": c.tr_nubar, "M": np.array(c.M[:]), "M_vac": c.M_vac,
+            "dP_max": c.dP_max, "dP_mean": c.dP_mean, "step": c.step}
+
+
+def cosenu_set_stage_timing(h, on=True):
+    return _check(h, load().cosenu_set_stage_timing(h, 1 if on else 0))
+
+
+def cosenu_stage_times(h):
+    """(ms[4], launches[4]) summed per RK4 stage since the last call."""
+    ms = np.zeros(4)
+    n = (ctypes.c_int64 * 4)()
+    _check(h, load().cosenu_stage_times(h, _dptr(ms), n))
+    return ms, np.array(n[:], dtype=np.int64)
+
+
+def cosenu_steps_taken(h):
+    return int(load().cosenu_steps_taken(h))
+
+
+def cosenu_last_error(h=None):
+    return load().cosenu_last_error(h).decode()
+
+
+def cosenu_kernel_launches():
+    return int(load().cosenu_kernel_launches())
+
+
+# ---------------------------------------------------------------- owner object
+
+class Solver:
+    """Owns one handle: Solver(nz, nv, L, scheme, precision, **params)."""
+
+    def __init__(self, nz, nv, L, scheme=COSENU_FDKO, precision=COSENU_FP64, **params):
+        self.nz, self.nv, self.L = int(nz), int(nv), float(L)
+        self.h = cosenu_create(nz, nv, L, scheme, precision)
+        if params:
+            cosenu_set_params(self.h, **params)
+
+    def close(self):
+        if self.h:
+            cosenu_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_state(self, host):
+        cosenu_set_state(self.h, host)
+
+    def state(self):
+        out = np.empty((2, 4, self.nz, self.nv))
+        cosenu_get_state(self.h, out)
+        return out
+
+    def rows(self, z0, nrows):
+        out = np.empty((2, 4, nrows, self.nv))
+        cosenu_get_rows(self.h, z0, nrows, out)
+        return out
+
+    def step(self, n=1):
+        cosenu_step(self.h, n)
+
+    def sync(self):
+        cosenu_sync(self.h)
+
+    def moments(self):
+        zavg = np.empty((2, 4, self.nv))
+        vmom = np.empty((self.nz, 6))
+        cosenu_moments(self.h, zavg, vmom)
+        return zavg, vmom
+
+    def conserved(self):
+        return cosenu_conserved(self.h)
+
+    @property
+    def params(self):
+        p = cosenu_get_params(self.h)
+        return {"mu": p.mu, "omega": p.omega, "theta": p.theta, "lambda": p.lambda_,
+                "ko_eps": p.ko_eps, "weno_eps": p.weno_eps, "dt": p.dt}

@@ -1,0 +1,594 @@
+// C ABI of the COSEnu GB300 engine (declared in include/cosenu.h).
+//
+// A handle owns one solver: the state in two ping-pong buffers (stage 4 reads
+// the old state with a halo while writing the new one), the three RK4 stage
+// increments, the per-z running moments of the mixed path, and a small
+// reduction scratch area.  cosenu_step() enqueues four fused stage kernels per
+// RK4 step on the handle's stream; pairs of steps are replayed from a CUDA
+// graph when the stream allows capture.
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/cosenu.h"
+#include "diag_kernels.cuh"
+#include "stage_launch.cuh"
+
+using namespace cosenu;
+
+namespace {
+
+std::atomic<uint64_t> g_launches{0};
+thread_local std::string tl_error;
+
+constexpr size_t kAlign = 256;
+constexpr int64_t kMinRowsPerCta = 16;
+constexpr int kSmemLimit = 232448;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+struct StageCfg {
+  int grid = 0, block = 0, ring = 0, slot_bytes = 0;
+  int64_t rows = 0;
+  size_t smem = 0;
+};
+
+struct Layout {
+  size_t y0, y1, d1, d2, d3, my, zavg, partial, result, err, total;
+};
+
+bool valid_sizes(int64_t nz, int32_t nv, int scheme, int precision) {
+  return nz >= 1 && nv >= 4 && nv <= 256 && nv % 4 == 0 &&
+         (scheme == COSENU_FDKO || scheme == COSENU_WENO7) &&
+         (precision == COSENU_FP64 || precision == COSENU_MIXED) &&
+         nz <= ((int64_t)1 << 40) / ((int64_t)8 * nv);
+}
+
+Layout make_layout(int64_t nz, int32_t nv, int precision) {
+  Layout L;
+  const size_t n = (size_t)8 * nz * nv;
+  const size_t dsz = precision == COSENU_FP64 ? sizeof(double) : sizeof(float);
+  size_t off = 0;
+  L.y0 = off; off = align_up(off + n * sizeof(double));
+  L.y1 = off; off = align_up(off + n * sizeof(double));
+  L.d1 = off; off = align_up(off + n * dsz);
+  L.d2 = off; off = align_up(off + n * dsz);
+  L.d3 = off; off = align_up(off + n * dsz);
+  L.my = off; off = align_up(off + (size_t)nz * 8 * sizeof(double));
+  L.zavg = off; off = align_up(off + (size_t)8 * nv * sizeof(double));
+  L.partial = off; off = align_up(off + (size_t)kDiagMaxBlocks * 8 * sizeof(double));
+  L.result = off; off = align_up(off + 8 * sizeof(double));
+  L.err = off; off = align_up(off + 64);
+  L.total = off;
+  return L;
+}
+
+}  // namespace
+
+struct cosenu_s {
+  int64_t nz = 0;
+  int32_t nv = 0;
+  double L = 0;
+  int scheme = 0, precision = 0;
+  cosenu_params p{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  bool own_mem = false;
+  unsigned char* ws = nullptr;
+  Layout lay{};
+  double* y[2] = {nullptr, nullptr};
+  int ycur = 0;
+  void* d[3] = {nullptr, nullptr, nullptr};
+  double* my = nullptr;
+  uint32_t* err = nullptr;
+  StageCfg cfg[5];
+  cudaGraphExec_t graph = nullptr;  // two RK4 steps starting from y[0]
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_free;                    // reusable events
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[5];  // per stage: (start, stop)
+  int64_t steps = 0;
+  std::string error;
+};
+
+namespace {
+
+int fail(cosenu_t h, int code, const std::string& msg) {
+  if (h)
+    h->error = msg;
+  else
+    tl_error = msg;
+  return code;
+}
+
+int cuda_fail(cosenu_t h, cudaError_t e, const char* what) {
+  return fail(h, COSENU_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(h, call)                                  \
+  do {                                               \
+    cudaError_t e_ = (call);                         \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+  } while (0)
+
+cudaError_t launch_stage(cosenu_t h, int stage, const StageArgs& a) {
+  const StageCfg& c = h->cfg[stage];
+  cudaError_t e;
+  if (h->scheme == COSENU_FDKO && h->precision == COSENU_FP64)
+    e = launch_rk4_stage<kFDKO, kFP64>(stage, a, c.grid, c.block, c.smem, h->stream);
+  else if (h->scheme == COSENU_FDKO)
+    e = launch_rk4_stage<kFDKO, kMIXED>(stage, a, c.grid, c.block, c.smem, h->stream);
+  else if (h->precision == COSENU_FP64)
+    e = launch_rk4_stage<kWENO7, kFP64>(stage, a, c.grid, c.block, c.smem, h->stream);
+  else
+    e = launch_rk4_stage<kWENO7, kMIXED>(stage, a, c.grid, c.block, c.smem, h->stream);
+  if (e == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
+  return e;
+}
+
+int max_blocks(cosenu_t h, int stage, int block, size_t smem) {
+  if (h->scheme == COSENU_FDKO && h->precision == COSENU_FP64)
+    return stage_max_blocks_per_sm<kFDKO, kFP64>(stage, block, smem);
+  if (h->scheme == COSENU_FDKO) return stage_max_blocks_per_sm<kFDKO, kMIXED>(stage, block, smem);
+  if (h->precision == COSENU_FP64)
+    return stage_max_blocks_per_sm<kWENO7, kFP64>(stage, block, smem);
+  return stage_max_blocks_per_sm<kWENO7, kMIXED>(stage, block, smem);
+}
+
+int slot_bytes(cosenu_t h, int stage) {
+  return h->precision == COSENU_FP64 ? slot_layout<kFP64>(h->nv, stage).bytes
+                                     : slot_layout<kMIXED>(h->nv, stage).bytes;
+}
+
+// Launch shape of each stage: one thread per (species, v) column; the ring
+// depth that gives the most resident CTAs per SM (then the deepest ring);
+// a persistent grid of at most (SMs x resident CTAs) CTAs with contiguous z
+// ranges of at least kMinRowsPerCta rows.
+int configure(cosenu_t h) {
+  int dev = 0, nsm = 0;
+  CK(h, cudaGetDevice(&dev));
+  CK(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  const int header = h->precision == COSENU_FP64 ? stage_smem_header_bytes<kFP64>()
+                                                 : stage_smem_header_bytes<kMIXED>();
+  for (int s = 1; s <= 4; ++s) {
+    StageCfg c;
+    c.block = ((2 * h->nv + 31) / 32) * 32;
+    c.slot_bytes = slot_bytes(h, s);
+    int best_occ = 0, best_d = 0;
+    for (int D = 2; D <= 8; ++D) {
+      const size_t smem = (size_t)header + (size_t)D * c.slot_bytes;
+      if (smem > (size_t)kSmemLimit) break;
+      const int occ = max_blocks(h, s, c.block, smem);
+      if (occ < 0) return fail(h, COSENU_ECUDA, "occupancy query failed");
+      if (occ <= 0) continue;
+      // prefer more resident CTAs while the ring stays at least 3 deep
+      const bool better = (occ > best_occ && (D >= 3 || best_d < 3)) ||
+                          (occ == best_occ && D > best_d) || best_d == 0;
+      if (better) {
+        best_occ = occ;
+        best_d = D;
+      }
+    }
+    if (best_d == 0) return fail(h, COSENU_EINVAL, "grid row does not fit in shared memory");
+    c.ring = best_d;
+    c.smem = (size_t)header + (size_t)best_d * c.slot_bytes;
+    const int64_t max_grid = (int64_t)nsm * best_occ;
+    int64_t grid = (h->nz + kMinRowsPerCta - 1) / kMinRowsPerCta;
+    if (grid > max_grid) grid = max_grid;
+    if (grid < 1) grid = 1;
+    c.rows = (h->nz + grid - 1) / grid;
+    c.grid = (int)((h->nz + c.rows - 1) / c.rows);
+    h->cfg[s] = c;
+  }
+  return COSENU_OK;
+}
+
+StageArgs stage_args(cosenu_t h, int stage, int ycur) {
+  StageArgs a;
+  std::memset(&a, 0, sizeof(a));
+  a.nz = h->nz;
+  a.nv = h->nv;
+  a.ncols = 2 * h->nv;
+  a.rows_per_cta = h->cfg[stage].rows;
+  a.ring = h->cfg[stage].ring;
+  a.slot_bytes = h->cfg[stage].slot_bytes;
+  a.inv_dz = (double)h->nz / h->L;
+  a.dt = h->p.dt;
+  a.mu = h->p.mu;
+  a.hvac_d = -h->p.omega * std::cos(2.0 * h->p.theta);
+  a.hvac_r = 0.5 * h->p.omega * std::sin(2.0 * h->p.theta);
+  a.lambda = h->p.lambda;
+  a.ko_eps = h->p.ko_eps;
+  a.weno_eps = h->p.weno_eps;
+  a.y_in = h->y[ycur];
+  a.y_out = h->y[ycur ^ 1];
+  a.my = h->my;
+  a.err = h->err;
+  switch (stage) {
+    case 1: a.d_out = h->d[0]; break;
+    case 2: a.d_in = h->d[0]; a.d_out = h->d[1]; break;
+    case 3: a.d_in = h->d[1]; a.d_out = h->d[2]; break;
+    default: a.d_in = h->d[2]; a.d1 = h->d[0]; a.d2 = h->d[1]; break;
+  }
+  return a;
+}
+
+cudaError_t take_event(cosenu_t h, cudaEvent_t* out) {
+  if (!h->ev_free.empty()) {
+    *out = h->ev_free.back();
+    h->ev_free.pop_back();
+    return cudaSuccess;
+  }
+  return cudaEventCreate(out);
+}
+
+cudaError_t enqueue_step(cosenu_t h, int ycur) {
+  for (int s = 1; s <= 4; ++s) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (h->timing) {
+      cudaError_t e = take_event(h, &e0);
+      if (e == cudaSuccess) e = take_event(h, &e1);
+      if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+      if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = launch_stage(h, s, stage_args(h, s, ycur));
+    if (e != cudaSuccess) return e;
+    if (h->timing) {
+      e = cudaEventRecord(e1, h->stream);
+      if (e != cudaSuccess) return e;
+      h->ev[s].push_back({e0, e1});
+    }
+  }
+  return cudaSuccess;
+}
+
+void drop_graph(cosenu_t h) {
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  h->graph = nullptr;
+}
+
+// Capture two RK4 steps starting from y[0] (they end in y[0] again).
+int build_graph(cosenu_t h) {
+  if (h->stream == nullptr) return COSENU_OK;  // the legacy stream cannot be captured
+  cudaGraph_t g = nullptr;
+  CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+  const uint64_t before = g_launches.load();
+  cudaError_t e = enqueue_step(h, 0);
+  if (e == cudaSuccess) e = enqueue_step(h, 1);
+  cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
+  g_launches.store(before);  // captured launches run later, counted per replay
+  if (e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    return cuda_fail(h, e, "stage launch during capture");
+  }
+  if (e2 != cudaSuccess) return cuda_fail(h, e2, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&h->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    h->graph = nullptr;
+    return cuda_fail(h, e, "cudaGraphInstantiate");
+  }
+  return COSENU_OK;
+}
+
+void default_params(cosenu_t h) {
+  h->p.mu = 1.0;
+  h->p.omega = 0.0;
+  h->p.theta = 0.0;
+  h->p.lambda = 0.0;
+  h->p.ko_eps = 0.1;
+  h->p.weno_eps = 1e-6;
+  h->p.dt = 0.4 * h->L / (double)h->nz;
+}
+
+cosenu_t create_common(int64_t nz, int32_t nv, double L, int scheme, int precision,
+                       void* workspace, size_t ws_bytes) {
+  if (!valid_sizes(nz, nv, scheme, precision) || !(L > 0.0) || !std::isfinite(L)) {
+    fail(nullptr, COSENU_EINVAL,
+         "invalid grid: need nz >= 1, 4 <= nv <= 256, nv % 4 == 0, L > 0, known scheme/precision");
+    return nullptr;
+  }
+  cosenu_t h = new (std::nothrow) cosenu_s;
+  if (!h) {
+    fail(nullptr, COSENU_ENOMEM, "host allocation failed");
+    return nullptr;
+  }
+  h->nz = nz;
+  h->nv = nv;
+  h->L = L;
+  h->scheme = scheme;
+  h->precision = precision;
+  default_params(h);
+  h->lay = make_layout(nz, nv, precision);
+  auto bail = [&](const std::string& why, int code) -> cosenu_t {
+    fail(nullptr, code, why + (h->error.empty() ? "" : (": " + h->error)));
+    if (h->own_mem && h->ws) cudaFree(h->ws);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+    return nullptr;
+  };
+  if (workspace) {
+    if (ws_bytes < h->lay.total || ((uintptr_t)workspace % kAlign) != 0)
+      return bail("workspace too small or not 256-byte aligned", COSENU_EINVAL);
+    h->ws = static_cast<unsigned char*>(workspace);
+  } else {
+    cudaError_t e = cudaMalloc(&h->ws, h->lay.total);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      h->ws = nullptr;
+      return bail(std::string("cudaMalloc of the workspace failed: ") + cudaGetErrorString(e),
+                  COSENU_ENOMEM);
+    }
+    h->own_mem = true;
+  }
+  cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return bail(std::string("stream: ") + cudaGetErrorString(e), COSENU_ECUDA);
+  h->own_stream = true;
+  h->y[0] = reinterpret_cast<double*>(h->ws + h->lay.y0);
+  h->y[1] = reinterpret_cast<double*>(h->ws + h->lay.y1);
+  h->d[0] = h->ws + h->lay.d1;
+  h->d[1] = h->ws + h->lay.d2;
+  h->d[2] = h->ws + h->lay.d3;
+  h->my = reinterpret_cast<double*>(h->ws + h->lay.my);
+  h->err = reinterpret_cast<uint32_t*>(h->ws + h->lay.err);
+  if (configure(h) != COSENU_OK) return bail("launch configuration failed", COSENU_ECUDA);
+  e = cudaMemsetAsync(h->ws, 0, h->lay.total, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return bail(std::string("memset: ") + cudaGetErrorString(e), COSENU_ECUDA);
+  return h;
+}
+
+// Recompute the running FP64 moments of y after the state was replaced.
+cudaError_t refresh_moments(cosenu_t h) {
+  ymoments_kernel<<<(int)std::min<int64_t>((h->nz + 7) / 8, 65535), 256, 0, h->stream>>>(
+      h->y[h->ycur], h->nz, h->nv, h->my, 8);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaGetLastError();
+}
+
+int check_n(cosenu_t h, size_t n) {
+  if ((int64_t)n != 8 * h->nz * (int64_t)h->nv)
+    return fail(h, COSENU_EINVAL, "state length must be 8 * nz * nv");
+  return COSENU_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t cosenu_workspace_bytes(int64_t nz, int32_t nv, int scheme, int precision) {
+  if (!valid_sizes(nz, nv, scheme, precision)) return 0;
+  return make_layout(nz, nv, precision).total;
+}
+
+cosenu_t cosenu_create(int64_t nz, int32_t nv, double L, int scheme, int precision) {
+  return create_common(nz, nv, L, scheme, precision, nullptr, 0);
+}
+
+cosenu_t cosenu_create_external(int64_t nz, int32_t nv, double L, int scheme, int precision,
+                                void* workspace, size_t workspace_bytes) {
+  if (!workspace) {
+    fail(nullptr, COSENU_EINVAL, "workspace is NULL");
+    return nullptr;
+  }
+  return create_common(nz, nv, L, scheme, precision, workspace, workspace_bytes);
+}
+
+void cosenu_destroy(cosenu_t h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  drop_graph(h);
+  for (int s = 1; s <= 4; ++s)
+    for (auto& pr : h->ev[s]) {
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+  for (cudaEvent_t e : h->ev_free) cudaEventDestroy(e);
+  if (h->own_mem && h->ws) cudaFree(h->ws);
+  if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+int cosenu_set_params(cosenu_t h, const cosenu_params* p) {
+  if (!h || !p) return fail(h, COSENU_EINVAL, "NULL argument");
+  const double vals[7] = {p->mu, p->omega, p->theta, p->lambda, p->ko_eps, p->weno_eps, p->dt};
+  for (double x : vals)
+    if (!std::isfinite(x)) return fail(h, COSENU_EINVAL, "parameters must be finite");
+  if (p->weno_eps <= 0.0) return fail(h, COSENU_EINVAL, "weno_eps must be positive");
+  if (p->ko_eps < 0.0) return fail(h, COSENU_EINVAL, "ko_eps must be non-negative");
+  h->p = *p;
+  if (h->p.dt <= 0.0) h->p.dt = 0.4 * h->L / (double)h->nz;
+  drop_graph(h);
+  return COSENU_OK;
+}
+
+int cosenu_get_params(cosenu_t h, cosenu_params* p) {
+  if (!h || !p) return fail(h, COSENU_EINVAL, "NULL argument");
+  *p = h->p;
+  return COSENU_OK;
+}
+
+int cosenu_set_stream(cosenu_t h, void* stream) {
+  if (!h) return fail(h, COSENU_EINVAL, "NULL handle");
+  CK(h, cudaStreamSynchronize(h->stream));
+  drop_graph(h);
+  if (h->own_stream) cudaStreamDestroy(h->stream);
+  h->own_stream = false;
+  h->stream = static_cast<cudaStream_t>(stream);
+  return COSENU_OK;
+}
+
+int cosenu_set_state(cosenu_t h, const double* host, size_t n) {
+  if (!h || !host) return fail(h, COSENU_EINVAL, "NULL argument");
+  if (int rc = check_n(h, n)) return rc;
+  h->ycur = 0;
+  CK(h, cudaMemcpyAsync(h->y[0], host, n * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  CK(h, refresh_moments(h));
+  CK(h, cudaMemsetAsync(h->err, 0, 64, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  h->steps = 0;
+  return COSENU_OK;
+}
+
+int cosenu_set_state_device(cosenu_t h, const double* dev, size_t n) {
+  if (!h || !dev) return fail(h, COSENU_EINVAL, "NULL argument");
+  if (int rc = check_n(h, n)) return rc;
+  h->ycur = 0;
+  CK(h, cudaMemcpyAsync(h->y[0], dev, n * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  CK(h, refresh_moments(h));
+  CK(h, cudaMemsetAsync(h->err, 0, 64, h->stream));
+  h->steps = 0;
+  return COSENU_OK;
+}
+
+int cosenu_get_state(cosenu_t h, double* host, size_t n) {
+  if (!h || !host) return fail(h, COSENU_EINVAL, "NULL argument");
+  if (int rc = check_n(h, n)) return rc;
+  CK(h, cudaMemcpyAsync(host, h->y[h->ycur], n * sizeof(double), cudaMemcpyDeviceToHost,
+                        h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return COSENU_OK;
+}
+
+int cosenu_get_rows(cosenu_t h, int64_t z0, int64_t nrows, double* host) {
+  if (!h || !host) return fail(h, COSENU_EINVAL, "NULL argument");
+  if (z0 < 0 || nrows < 0 || z0 + nrows > h->nz) return fail(h, COSENU_EINVAL, "rows out of range");
+  if (nrows == 0) return COSENU_OK;
+  const size_t rowb = (size_t)h->nv * sizeof(double);
+  // 8 planes of nz rows -> 8 blocks of nrows rows
+  CK(h, cudaMemcpy2DAsync(host, nrows * rowb, h->y[h->ycur] + z0 * h->nv, h->nz * rowb,
+                          nrows * rowb, 8, cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return COSENU_OK;
+}
+
+const double* cosenu_state_device(cosenu_t h) { return h ? h->y[h->ycur] : nullptr; }
+
+int cosenu_step(cosenu_t h, int64_t nsteps) {
+  if (!h) return fail(h, COSENU_EINVAL, "NULL handle");
+  if (nsteps < 0) return fail(h, COSENU_EINVAL, "nsteps must be >= 0");
+  int64_t left = nsteps;
+  if (left >= 2 && !h->graph && h->stream && !h->timing) {
+    if (int rc = build_graph(h)) return rc;
+  }
+  if (left >= 2 && h->graph && !h->timing) {
+    if (h->ycur == 1) {  // the graph starts from y[0]
+      CK(h, enqueue_step(h, 1));
+      h->ycur = 0;
+      --left;
+    }
+    for (; left >= 2; left -= 2) {
+      CK(h, cudaGraphLaunch(h->graph, h->stream));
+      g_launches.fetch_add(8, std::memory_order_relaxed);
+    }
+  }
+  for (; left > 0; --left) {
+    CK(h, enqueue_step(h, h->ycur));
+    h->ycur ^= 1;
+  }
+  h->steps += nsteps;
+  return COSENU_OK;
+}
+
+int cosenu_sync(cosenu_t h) {
+  if (!h) return fail(h, COSENU_EINVAL, "NULL handle");
+  uint32_t flags = 0;
+  CK(h, cudaMemcpyAsync(&flags, h->err, sizeof(flags), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  if (flags) {
+    CK(h, cudaMemsetAsync(h->err, 0, 64, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (flags & kErrTimeout) return fail(h, COSENU_ETIMEOUT, "a device-side wait gave up");
+    return fail(h, COSENU_ENONFINITE, "non-finite value in the state");
+  }
+  return COSENU_OK;
+}
+
+int cosenu_moments(cosenu_t h, double* zavg, double* vmom) {
+  if (!h) return fail(h, COSENU_EINVAL, "NULL handle");
+  const double* y = h->y[h->ycur];
+  if (zavg) {
+    double* dz = reinterpret_cast<double*>(h->ws + h->lay.zavg);
+    zavg_kernel<<<dim3((h->nv + 31) / 32, 8), 256, 0, h->stream>>>(y, h->nz, h->nv, dz);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    CK(h, cudaGetLastError());
+    CK(h, cudaMemcpyAsync(zavg, dz, (size_t)8 * h->nv * sizeof(double), cudaMemcpyDeviceToHost,
+                          h->stream));
+  }
+  if (vmom) {
+    // staged in the delta_1 buffer (free between steps), row stride 8
+    double* dm = reinterpret_cast<double*>(h->d[0]);
+    ymoments_kernel<<<(int)std::min<int64_t>((h->nz + 7) / 8, 65535), 256, 0, h->stream>>>(
+        y, h->nz, h->nv, dm, 8);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    CK(h, cudaGetLastError());
+    CK(h, cudaMemcpy2DAsync(vmom, 6 * sizeof(double), dm, 8 * sizeof(double), 6 * sizeof(double),
+                            (size_t)h->nz, cudaMemcpyDeviceToHost, h->stream));
+  }
+  CK(h, cudaStreamSynchronize(h->stream));
+  return COSENU_OK;
+}
+
+int cosenu_conserved(cosenu_t h, cosenu_conserved_t* out) {
+  if (!h || !out) return fail(h, COSENU_EINVAL, "NULL argument");
+  const int64_t ncell = h->nz * h->nv;
+  const int nb = (int)std::min<int64_t>(kDiagMaxBlocks, (ncell + kDiagBlock - 1) / kDiagBlock);
+  double* part = reinterpret_cast<double*>(h->ws + h->lay.partial);
+  double* res = reinterpret_cast<double*>(h->ws + h->lay.result);
+  conserved_partial_kernel<<<nb, kDiagBlock, 0, h->stream>>>(h->y[h->ycur], h->nz, h->nv, part);
+  CK(h, cudaGetLastError());
+  conserved_final_kernel<<<1, 32, 0, h->stream>>>(part, nb, res);
+  CK(h, cudaGetLastError());
+  g_launches.fetch_add(2, std::memory_order_relaxed);
+  double r[8];
+  CK(h, cudaMemcpyAsync(r, res, sizeof(r), cudaMemcpyDeviceToHost, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  const double w = (2.0 / h->nv) * (h->L / (double)h->nz);
+  out->tr_nu = w * r[0];
+  out->tr_nubar = w * r[1];
+  out->M[0] = w * r[2];
+  out->M[1] = w * r[3];
+  out->M[2] = w * r[4];
+  out->M_vac = std::sin(2.0 * h->p.theta) * out->M[0] - std::cos(2.0 * h->p.theta) * out->M[2];
+  out->dP_max = r[5];
+  out->dP_mean = r[7] > 0.0 ? r[6] / r[7] : 0.0;
+  out->step = h->steps;
+  return COSENU_OK;
+}
+
+int cosenu_set_stage_timing(cosenu_t h, int on) {
+  if (!h) return fail(h, COSENU_EINVAL, "NULL handle");
+  h->timing = on != 0;
+  return COSENU_OK;
+}
+
+int cosenu_stage_times(cosenu_t h, double* ms, int64_t* n) {
+  if (!h) return fail(h, COSENU_EINVAL, "NULL handle");
+  CK(h, cudaStreamSynchronize(h->stream));
+  for (int s = 1; s <= 4; ++s) {
+    double sum = 0.0;
+    for (auto& pr : h->ev[s]) {
+      float t = 0.0f;
+      CK(h, cudaEventElapsedTime(&t, pr.first, pr.second));
+      sum += t;
+      h->ev_free.push_back(pr.first);
+      h->ev_free.push_back(pr.second);
+    }
+    if (ms) ms[s - 1] = sum;
+    if (n) n[s - 1] = (int64_t)h->ev[s].size();
+    h->ev[s].clear();
+  }
+  return COSENU_OK;
+}
+
+int64_t cosenu_steps_taken(cosenu_t h) { return h ? h->steps : -1; }
+
+const char* cosenu_last_error(cosenu_t h) {
+  return h ? h->error.c_str() : tl_error.c_str();
+}
+
+uint64_t cosenu_kernel_launches(void) { return g_launches.load(); }
+
+}  // extern "C"

@@ -1,0 +1,154 @@
+// Device-side building blocks of the COSEnu GB300 kernels: mbarrier and
+// bulk-copy (TMA) wrappers with bounded waits, warp reductions, and the
+// argument block shared by the stage kernels and their launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cosenu {
+
+constexpr int kFDKO = 0;
+constexpr int kWENO7 = 1;
+constexpr int kFP64 = 0;
+constexpr int kMIXED = 1;
+
+// Device error bits (OR-ed into the handle's flag word).
+constexpr uint32_t kErrNonFinite = 1u;
+constexpr uint32_t kErrTimeout = 2u;
+
+// A bounded wait gives up after this many SM clock cycles (about 2 s).
+constexpr long long kWaitLimitCycles = 4000000000LL;
+
+// Ring of moment slots per CTA; must exceed the stencil lag (2 or 4 rows).
+constexpr int kMomSlots = 8;
+constexpr int kMaxWarps = 16;  // 2 * nv / 32 with nv <= 256
+
+// Arguments of one RK4 stage launch.  All arrays use the layout
+// [8 = species*4 + component][nz][nv]; Delta is double (FP64) or float (mixed).
+struct StageArgs {
+  int64_t nz;
+  int32_t nv;
+  int32_t ncols;          // 2 * nv active threads
+  int64_t rows_per_cta;   // contiguous z rows owned by each CTA
+  int32_t ring;           // bulk-copy ring depth (rows in flight)
+  int32_t slot_bytes;     // bytes of one ring slot
+  double inv_dz;          // 1 / dz
+  double dt;
+  double mu;
+  double hvac_d;          // -omega cos(2 theta): (H_vac)_ee - (H_vac)_xx
+  double hvac_r;          // (omega / 2) sin(2 theta): Re (H_vac)_ex
+  double lambda;          // matter potential (nu: +, nubar: -)
+  double ko_eps;
+  double weno_eps;
+  const double* y_in;     // state at the start of the step (read with halo)
+  double* y_out;          // stage 4: state at the end of the step
+  const void* d_in;       // stage s > 1: delta_{s-1} (read with halo)
+  void* d_out;            // stages 1-3: delta_s
+  const void* d1;         // stage 4: delta_1 (center rows only)
+  const void* d2;         // stage 4: delta_2 (center rows only)
+  double* my;             // mixed: running FP64 moments of y, [nz][8] (6 used)
+  uint32_t* err;          // device error flags
+};
+
+// ------------------------------------------------------------------ PTX
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Wait for phase `parity` of the barrier, giving up after kWaitLimitCycles.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_try_wait(bar, parity)) {
+    if (clock64() - t0 > kWaitLimitCycles) return false;
+  }
+  return true;
+}
+
+// Bulk copy (TMA, non-tensor) of `bytes` from global to this CTA's shared
+// memory; completion is counted on the mbarrier.  src, dst 16-B aligned,
+// bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes,
+                                         uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+// ------------------------------------------------------------------ reductions
+
+// Sum six per-lane values over the 32 lanes of a warp with the transposing
+// butterfly: 9 shuffles and 9 adds per lane instead of 30.  On return, lane L
+// holds the warp total of value k = (L >> 2) & 7 (k < 6 meaningful).
+template <typename T>
+__device__ __forceinline__ T warp_sum6_transposed(const T (&m)[6]) {
+  const int lane = threadIdx.x & 31;
+  T a[8] = {m[0], m[1], m[2], m[3], m[4], m[5], T(0), T(0)};
+  // level 1: keep half 0..3 (bit 4 clear) or 4..7 (bit 4 set)
+  T b[4];
+  const bool up16 = lane & 16;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const T send = up16 ? a[k] : a[k + 4];
+    const T keep = up16 ? a[k + 4] : a[k];
+    b[k] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+  T c[2];
+  const bool up8 = lane & 8;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const T send = up8 ? b[k] : b[k + 2];
+    const T keep = up8 ? b[k + 2] : b[k];
+    c[k] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  const bool up4 = lane & 4;
+  T d;
+  {
+    const T send = up4 ? c[0] : c[1];
+    const T keep = up4 ? c[1] : c[0];
+    d = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+  }
+  d += __shfl_xor_sync(0xffffffffu, d, 2);
+  d += __shfl_xor_sync(0xffffffffu, d, 1);
+  return d;
+}
+
+__device__ __forceinline__ bool is_finite_bits(double x) {
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(x));
+  return ((b >> 52) & 0x7ffull) != 0x7ffull;
+}
+
+}  // namespace cosenu

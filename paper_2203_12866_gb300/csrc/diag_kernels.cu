@@ -1,0 +1,138 @@
+// Reduction kernels of the COSEnu engine: per-z velocity moments of the state,
+// z-averages, and the conserved-quantity diagnostics (arXiv:2203.12866, Sec. 2
+// for P0 and |P|, Sec. 5 for M_0 and delta P).  All reductions run in double
+// in a fixed order, so repeated calls on the same state give the same bits.
+#include "diag_kernels.cuh"
+
+namespace cosenu {
+
+// D_n = sum_j dv v_j^n (S_j - Sbar_j^*) of every z row, n = 0, 1 (Eq. (ham)).
+// One warp per row; lanes stride over v.  out[z * stride + k], k < 6.
+__global__ void ymoments_kernel(const double* __restrict__ y, int64_t nz, int nv,
+                                double* __restrict__ out, int stride) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const double dv = 2.0 / nv;
+  for (int64_t z = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); z < nz;
+       z += warps_total) {
+    double m[6] = {0, 0, 0, 0, 0, 0};
+    for (int j = lane; j < nv; j += 32) {
+      const double v = -1.0 + (j + 0.5) * dv;
+      auto at = [&](int q) { return y[((int64_t)q * nz + z) * nv + j]; };
+      const double d3 = (at(0) - at(1)) - (at(4) - at(5));
+      const double dr = at(2) - at(6);
+      const double di = at(3) + at(7);
+      m[0] += dv * d3;
+      m[1] += dv * v * d3;
+      m[2] += dv * dr;
+      m[3] += dv * v * dr;
+      m[4] += dv * di;
+      m[5] += dv * v * di;
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m[k] += __shfl_xor_sync(0xffffffffu, m[k], o);
+    }
+    if (lane < 6) {
+      double val = m[0];
+#pragma unroll
+      for (int k = 1; k < 6; ++k)
+        if (lane == k) val = m[k];
+      out[z * stride + lane] = val;
+    }
+    if (lane >= 6 && lane < stride) out[z * stride + lane] = 0.0;
+  }
+}
+
+// Column sums over z: out[q][v] = (1/nz) sum_z y[q][z][v].  Block = (q, 32 v);
+// 8 warps split z, partial sums combined in a fixed order.
+__global__ void zavg_kernel(const double* __restrict__ y, int64_t nz, int nv,
+                            double* __restrict__ out) {
+  __shared__ double part[8][32];
+  const int q = blockIdx.y;
+  const int j = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int w = threadIdx.x >> 5;
+  double acc = 0.0;
+  if (j < nv)
+    for (int64_t z = w; z < nz; z += 8) acc += y[((int64_t)q * nz + z) * nv + j];
+  part[w][threadIdx.x & 31] = acc;
+  __syncthreads();
+  if (w == 0 && j < nv) {
+    double s = 0.0;
+    for (int k = 0; k < 8; ++k) s += part[k][threadIdx.x & 31];
+    out[q * nv + j] = s / (double)nz;
+  }
+}
+
+// Per-block partial sums of the diagnostics over (z, v) cells:
+// [0] sum P0(nu) [1] sum P0(nubar) [2..4] sum P(S - Sbar^*) [5] max |dP|
+// [6] sum |dP_nu| P0_nu [7] sum P0_nu (cells with P0 > 0).
+__global__ void conserved_partial_kernel(const double* __restrict__ y, int64_t nz, int nv,
+                                         double* __restrict__ partial) {
+  __shared__ double red[8][kDiagBlock / 32];
+  const int64_t ncell = nz * nv;
+  double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ncell;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t z = e / nv, j = e % nv;
+    double P[2][4];
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+      const double a = y[((int64_t)(s * 4 + 0) * nz + z) * nv + j];
+      const double b = y[((int64_t)(s * 4 + 1) * nz + z) * nv + j];
+      const double cr = y[((int64_t)(s * 4 + 2) * nz + z) * nv + j];
+      const double ci = y[((int64_t)(s * 4 + 3) * nz + z) * nv + j];
+      P[s][0] = a + b;
+      P[s][1] = 2.0 * cr;
+      P[s][2] = -2.0 * ci;
+      P[s][3] = a - b;
+      if (P[s][0] > 0.0) {
+        const double len = sqrt(P[s][1] * P[s][1] + P[s][2] * P[s][2] + P[s][3] * P[s][3]);
+        const double dp = fabs(len / P[s][0] - 1.0);
+        acc[5] = fmax(acc[5], dp);
+        if (s == 0) {
+          acc[6] += dp * P[s][0];
+          acc[7] += P[s][0];
+        }
+      }
+    }
+    acc[0] += P[0][0];
+    acc[1] += P[1][0];
+    acc[2] += P[0][1] - P[1][1];
+    acc[3] += P[0][2] + P[1][2];  // conjugation flips P2 of Sbar
+    acc[4] += P[0][3] - P[1][3];
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double other = __shfl_xor_sync(0xffffffffu, acc[k], o);
+      acc[k] = (k == 5) ? fmax(acc[k], other) : acc[k] + other;
+    }
+    if (lane == 0) red[k][w] = acc[k];
+  }
+  __syncthreads();
+  if (threadIdx.x < 8) {
+    const int k = threadIdx.x;
+    double s = red[k][0];
+    for (int i = 1; i < kDiagBlock / 32; ++i) s = (k == 5) ? fmax(s, red[k][i]) : s + red[k][i];
+    partial[(int64_t)blockIdx.x * 8 + k] = s;
+  }
+}
+
+// Sum the per-block partials in block order (one thread per quantity).
+__global__ void conserved_final_kernel(const double* __restrict__ partial, int nblocks,
+                                       double* __restrict__ out) {
+  const int k = threadIdx.x;
+  if (k >= 8) return;
+  double s = partial[k];
+  for (int b = 1; b < nblocks; ++b) {
+    const double x = partial[(int64_t)b * 8 + k];
+    s = (k == 5) ? fmax(s, x) : s + x;
+  }
+  out[k] = s;
+}
+
+}  // namespace cosenu

@@ -1,0 +1,21 @@
+// Declarations of the reduction kernels (diag_kernels.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cosenu {
+
+constexpr int kDiagBlock = 256;
+constexpr int kDiagMaxBlocks = 1024;
+
+__global__ void ymoments_kernel(const double* __restrict__ y, int64_t nz, int nv,
+                                double* __restrict__ out, int stride);
+__global__ void zavg_kernel(const double* __restrict__ y, int64_t nz, int nv,
+                            double* __restrict__ out);
+__global__ void conserved_partial_kernel(const double* __restrict__ y, int64_t nz, int nv,
+                                         double* __restrict__ partial);
+__global__ void conserved_final_kernel(const double* __restrict__ partial, int nblocks,
+                                       double* __restrict__ out);
+
+}  // namespace cosenu

@@ -1,0 +1,501 @@
+// Fused RK4 stage kernel of the COSEnu method (arXiv:2203.12866) for sm_103a.
+//
+// One launch computes one Runge-Kutta stage for the whole grid:
+//   u_s = y + delta_{s-1}                                   (stage input)
+//   k_s = -v d_z u_s  (FD4 + Kreiss-Oliger, Sec. 3.1, or FV WENO7, Sec. 3.2)
+//         - i [H(u_s), u_s]                                 (Eq. (eom), (ham))
+//   delta_1 = dt/2 k_1, delta_2 = dt/2 k_2, delta_3 = dt k_3,
+//   y <- y + (delta_1 + 2 delta_2 + delta_3) / 3 + dt/6 k_4   (classic RK4)
+//
+// Work decomposition.  A CTA owns a contiguous range of z rows and all 2 nv
+// (species, v) columns; thread t is column t.  The CTA marches along z: each
+// iteration one new row enters (bulk-copied by the TMA into a ring of shared
+// memory slots, several rows ahead), every thread keeps a sliding window of
+// its column in registers, and the row `lag` behind the leading one is
+// finished.  Because the CTA holds every v of a row, the velocity moments that
+// form H_nunu are reduced inside the CTA (warp shuffles, then a cross-warp sum
+// in shared memory) while the row waits to become the center.  Each stage
+// therefore reads the state once from HBM (plus a 2 x lag row halo per CTA)
+// and writes its output once.
+//
+// Moments.  H_nunu(v) = mu sum_j dv (1 - v v_j) [S_j - Sbar_j^*] is separable:
+// with D_n = sum_j dv v_j^n (S_j - Sbar_j^*), H_nunu(v) = mu (D_0 - v D_1).
+//  - FP64 path: D_n of u_s in double.
+//  - mixed path: D_n(u_s) = D_n(y) + D_n(delta_{s-1}).  D_n(y) is a per-z double
+//    running sum (set from y once, then advanced by D_n of each step's float
+//    increment in stage 4); D_n(delta) is summed in float.
+#pragma once
+
+#include "cosenu_device.cuh"
+
+namespace cosenu {
+
+template <int PREC>
+struct Prec;
+template <>
+struct Prec<kFP64> {
+  using Real = double;   // stencil / commutator arithmetic
+  using Delta = double;  // storage of stage increments
+};
+template <>
+struct Prec<kMIXED> {
+  using Real = float;
+  using Delta = float;
+};
+
+template <int SCHEME>
+struct Scheme;
+template <>
+struct Scheme<kFDKO> {
+  static constexpr int kLag = 2;  // center = leading row - 2
+  static constexpr int kWin = 5;  // rows c-2 .. c+2
+  static constexpr int kLo = 2;   // halo rows before the first center
+  static constexpr int kHi = 2;   // halo rows after the last center
+};
+template <>
+struct Scheme<kWENO7> {
+  static constexpr int kLag = 4;  // center = leading row - 4
+  static constexpr int kWin = 8;  // rows c-3 .. c+4 (face c+1/2 of either upwind side)
+  static constexpr int kLo = 4;   // face z_begin - 1/2 needs rows from z_begin - 4
+  static constexpr int kHi = 4;
+};
+
+// Byte layout of one ring slot.  Window arrays belong to the leading row i,
+// center arrays (stage 4 only) to the row i - lag.
+struct SlotLayout {
+  int y_off, din_off, yc_off, d1c_off, d2c_off, my_off, bytes;
+};
+
+template <int PREC>
+__host__ __device__ inline SlotLayout slot_layout(int nv, int stage) {
+  using Delta = typename Prec<PREC>::Delta;
+  SlotLayout L;
+  const int row_y = 8 * nv * (int)sizeof(double);
+  const int row_d = 8 * nv * (int)sizeof(Delta);
+  int off = 0;
+  L.y_off = off;
+  off += row_y;
+  L.din_off = off;
+  if (stage > 1) off += row_d;
+  L.yc_off = off;
+  if (stage == 4) off += row_y;
+  L.d1c_off = off;
+  if (stage == 4) off += row_d;
+  L.d2c_off = off;
+  if (stage == 4) off += row_d;
+  L.my_off = off;
+  if (PREC == kMIXED) off += 8 * (int)sizeof(double);
+  L.bytes = (off + 127) & ~127;
+  return L;
+}
+
+// Shared memory besides the ring: mbarriers, moment partials, finished moments.
+template <int PREC>
+__host__ __device__ inline int stage_smem_header_bytes() {
+  // mbarriers (16 x 8) | part[kMomSlots][kMaxWarps][8] double | partdy (same) |
+  // momf[kMomSlots][8] double | myring[kMomSlots][8] double | flags
+  return 128 + 2 * kMomSlots * kMaxWarps * 8 * 8 + 2 * kMomSlots * 8 * 8 + 128;
+}
+
+__device__ __forceinline__ int64_t wrap_row(int64_t r, int64_t nz) {
+  int64_t m = r % nz;
+  return m < 0 ? m + nz : m;
+}
+
+// ---------------------------------------------------------------- WENO7 face
+// Value at i+1/2 of the 7th-order WENO reconstruction from the cell values
+// f_{i-3..i+3} (Appendix A: sub-stencil values Eq. (f4s), smoothness indices
+// Eq. (Si4) as printed, weights Eq. (weight) with linear weights 4/35, 18/35,
+// 12/35, 1/35 for S_0 = {i..i+3} .. S_3 = {i-3..i}).
+
+template <typename R>
+__device__ __forceinline__ void weno7_parts(R fm3, R fm2, R fm1, R f0, R fp1, R fp2, R fp3,
+                                            R (&f4)[4], R (&si)[4]) {
+  const R c12 = R(1) / R(12);
+  f4[0] = (R(3) * f0 + R(13) * fp1 - R(5) * fp2 + fp3) * c12;
+  f4[1] = (-fm1 + R(7) * f0 + R(7) * fp1 - fp2) * c12;
+  f4[2] = (fm2 - R(5) * fm1 + R(13) * f0 + R(3) * fp1) * c12;
+  f4[3] = (R(-3) * fm3 + R(13) * fm2 - R(23) * fm1 + R(25) * f0) * c12;
+  si[0] = f0 * (R(2107) * f0 - R(9402) * fp1 + R(7042) * fp2 - R(1854) * fp3) +
+          fp1 * (R(11003) * fp1 - R(17246) * fp2 + R(4642) * fp3) +
+          fp2 * (R(7043) * fp2 - R(3882) * fp3) + R(547) * fp3 * fp3;
+  si[1] = fm1 * (R(547) * fm1 - R(2522) * f0 + R(1922) * fp1 - R(494) * fp2) +
+          f0 * (R(3443) * f0 - R(5966) * fp1 + R(1602) * fp2) +
+          fp1 * (R(2843) * fp1 - R(1642) * fp2) + R(267) * fp2 * fp2;
+  si[2] = fm2 * (R(267) * fm2 - R(1642) * fm1 + R(1602) * f0 - R(494) * fp1) +
+          fm1 * (R(2843) * fm1 - R(5966) * f0 + R(1922) * fp1) +
+          f0 * (R(3443) * f0 - R(2522) * fp1) + R(547) * fp1 * fp1;
+  si[3] = fm3 * (R(547) * fm3 - R(3882) * fm2 + R(4642) * fm1 - R(1854) * f0) +
+          fm2 * (R(7043) * fm2 - R(17246) * fm1 + R(7042) * f0) +
+          fm1 * (R(11003) * fm1 - R(9402) * f0) + R(2107) * f0 * f0;
+}
+
+// double: one division per face.  With q_r = (SI_r + eps)^2 the normalised
+// weights d_r / q_r / sum_k (d_k / q_k) equal d_r prod_{k!=r} q_k /
+// sum_j d_j prod_{k!=j} q_k (q_r >= eps^2 keeps the products in range).
+__device__ __forceinline__ double weno7_face(double fm3, double fm2, double fm1, double f0,
+                                             double fp1, double fp2, double fp3, double eps) {
+  double f4[4], si[4];
+  weno7_parts(fm3, fm2, fm1, f0, fp1, fp2, fp3, f4, si);
+  double q[4];
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const double t = si[r] + eps;
+    q[r] = t * t;
+  }
+  const double q01 = q[0] * q[1], q23 = q[2] * q[3];
+  const double a0 = (4.0 / 35.0) * (q[1] * q23);
+  const double a1 = (18.0 / 35.0) * (q[0] * q23);
+  const double a2 = (12.0 / 35.0) * (q01 * q[3]);
+  const double a3 = (1.0 / 35.0) * (q01 * q[2]);
+  const double num = a0 * f4[0] + a1 * f4[1] + a2 * f4[2] + a3 * f4[3];
+  return num / (a0 + a1 + a2 + a3);
+}
+
+// float: fast reciprocals (the mixed path's weights need no more).
+__device__ __forceinline__ float weno7_face(float fm3, float fm2, float fm1, float f0, float fp1,
+                                            float fp2, float fp3, float eps) {
+  float f4[4], si[4];
+  weno7_parts(fm3, fm2, fm1, f0, fp1, fp2, fp3, f4, si);
+  const float d[4] = {4.0f / 35.0f, 18.0f / 35.0f, 12.0f / 35.0f, 1.0f / 35.0f};
+  float w[4], ws = 0.0f, num = 0.0f;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const float t = si[r] + eps;
+    w[r] = __fdividef(d[r], t * t);
+    ws += w[r];
+    num += w[r] * f4[r];
+  }
+  return __fdividef(num, ws);
+}
+
+// ---------------------------------------------------------------- the kernel
+
+template <int SCHEME, int PREC, int STAGE>
+__global__ void __launch_bounds__(512, 1) rk4_stage_kernel(const StageArgs a) {
+  using Real = typename Prec<PREC>::Real;
+  using Delta = typename Prec<PREC>::Delta;
+  constexpr int LAG = Scheme<SCHEME>::kLag;
+  constexpr int WIN = Scheme<SCHEME>::kWin;
+  constexpr int LO = Scheme<SCHEME>::kLo;
+  constexpr int HI = Scheme<SCHEME>::kHi;
+
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);                           // [16]
+  double* part = reinterpret_cast<double*>(smem + 128);                         // [MS][W][8]
+  double* partdy = part + kMomSlots * kMaxWarps * 8;                            // [MS][W][8]
+  double* momf = partdy + kMomSlots * kMaxWarps * 8;                            // [MS][8]
+  double* myring = momf + kMomSlots * 8;                                        // [MS][8]
+  int* flags = reinterpret_cast<int*>(myring + kMomSlots * 8);                  // [32]
+  unsigned char* ring = smem + stage_smem_header_bytes<PREC>();
+
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  const int nwarps = blockDim.x >> 5;
+  const int64_t nz = a.nz;
+  const int nv = a.nv;
+  const SlotLayout L = slot_layout<PREC>(nv, STAGE);
+
+  const int64_t z_begin = (int64_t)blockIdx.x * a.rows_per_cta;
+  const int64_t z_end = min(nz, z_begin + a.rows_per_cta);
+  if (z_begin >= z_end) return;  // uniform over the CTA
+  const int64_t i_first = z_begin - LO;
+  const int64_t nrows = (z_end + HI) - i_first;
+  const int D = a.ring;
+
+  // ---- per-column constants
+  const bool active = tid < a.ncols;
+  const int s = active ? tid / nv : 0;  // species
+  const int vj = active ? tid % nv : 0;
+  const double dv = 2.0 / nv;
+  const double vd = -1.0 + (vj + 0.5) * dv;
+  const Real v = Real(vd);
+  const double sgn = (s == 0) ? 1.0 : -1.0;
+  // moment weights: D3 and Dr take + for nu and - for nubar, Di takes + for both
+  const Real w3 = active ? Real(sgn * dv) : Real(0);
+  const Real w3v = active ? Real(sgn * dv * vd) : Real(0);
+  const Real wi = active ? Real(dv) : Real(0);
+  const Real wiv = active ? Real(dv * vd) : Real(0);
+  // H = (hvac_d + sgn lambda + sgn mu (D3_0 - v D3_1), hvac_r + sgn mu (Dr_0 - v Dr_1),
+  //      mu (Di_0 - v Di_1)) for (H_ee - H_xx, Re H_ex, Im H_ex)
+  const Real hd0 = Real(a.hvac_d + sgn * a.lambda);
+  const Real hr0 = Real(a.hvac_r);
+  const Real mus = Real(sgn * a.mu);
+  const Real mu = Real(a.mu);
+  // advection coefficients
+  const Real c_fd = Real(-vd * a.inv_dz / 12.0);
+  const Real c_ko = Real(-a.ko_eps * a.inv_dz / 16.0);
+  const Real inv_dz = Real(a.inv_dz);
+  const Real eps_v = Real(a.weno_eps / (vd * vd));  // WENO_eps(v u) = v WENO_{eps/v^2}(u)
+  const bool upwind_left = vd > 0.0;
+  const Real dt = Real(a.dt);
+  const double dt_d = a.dt;
+
+  // ---- barriers and prologue copies
+  const uint32_t bar0 = smem_addr(bars);
+  if (tid == 0) {
+    for (int k = 0; k < D; ++k) mbar_init(bar0 + 8 * k, 1);
+    flags[0] = 0;
+    fence_barrier_init();
+  }
+  __syncthreads();
+
+  // Issue the copies of relative row j into its slot (producer thread only).
+  auto issue_row = [&](int64_t j) {
+    const int slot = (int)(j % D);
+    const uint32_t bar = bar0 + 8 * slot;
+    const uint32_t base = smem_addr(ring + (size_t)slot * a.slot_bytes);
+    const int64_t i = i_first + j;
+    const int64_t r = wrap_row(i, nz);
+    const int64_t c = i - LAG;
+    const bool has_center = (STAGE == 4) && c >= z_begin && c < z_end;
+    const bool has_my = (PREC == kMIXED) && i >= z_begin && i < z_end;
+    const uint32_t ry = nv * sizeof(double), rd = nv * sizeof(Delta);
+    uint32_t tx = 8 * ry + (STAGE > 1 ? 8 * rd : 0);
+    if (has_center) tx += 8 * ry + 16 * rd;
+    if (has_my) tx += 64;
+    mbar_arrive_expect_tx(bar, tx);
+    const Delta* din = static_cast<const Delta*>(a.d_in);
+#pragma unroll 1
+    for (int q = 0; q < 8; ++q) {
+      bulk_g2s(base + L.y_off + q * ry, a.y_in + ((int64_t)q * nz + r) * nv, ry, bar);
+      if (STAGE > 1) bulk_g2s(base + L.din_off + q * rd, din + ((int64_t)q * nz + r) * nv, rd, bar);
+    }
+    if (has_center) {
+      const Delta* d1 = static_cast<const Delta*>(a.d1);
+      const Delta* d2 = static_cast<const Delta*>(a.d2);
+#pragma unroll 1
+      for (int q = 0; q < 8; ++q) {
+        const int64_t o = ((int64_t)q * nz + c) * nv;
+        bulk_g2s(base + L.yc_off + q * ry, a.y_in + o, ry, bar);
+        bulk_g2s(base + L.d1c_off + q * rd, d1 + o, rd, bar);
+        bulk_g2s(base + L.d2c_off + q * rd, d2 + o, rd, bar);
+      }
+    }
+    if (has_my) bulk_g2s(base + L.my_off, a.my + i * 8, 64, bar);
+  };
+
+  if (tid == 0) {
+    const int64_t npro = nrows < (int64_t)D ? nrows : (int64_t)D;
+    for (int64_t j = 0; j < npro; ++j) issue_row(j);
+  }
+
+  // ---- per-thread window
+  Real u[WIN][4];
+#pragma unroll
+  for (int k = 0; k < WIN; ++k)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) u[k][q] = Real(0);
+  Real dring[LAG + 1][4];  // mixed stage 4: raw delta_3 of the last lag+1 rows
+#pragma unroll
+  for (int k = 0; k <= LAG; ++k)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) dring[k][q] = Real(0);
+  Real fprev[4] = {Real(0), Real(0), Real(0), Real(0)};  // WENO flux at c - 1/2
+  bool ok = true;
+  bool nonfinite = false;
+  int64_t jbreak = -1;
+
+#pragma unroll 1
+  for (int64_t j = 0; j < nrows; ++j) {
+    const int64_t i = i_first + j;
+    const int slot = (int)(j % D);
+    const unsigned char* sb = ring + (size_t)slot * a.slot_bytes;
+    const bool in_center_range_i = i >= z_begin && i < z_end;
+
+    if (ok && !mbar_wait_bounded(bar0 + 8 * slot, (uint32_t)((j / D) & 1))) {
+      ok = false;
+      atomicOr(a.err, kErrTimeout);
+      flags[0] = 1;
+    }
+
+    // ---- leading row i enters the window
+    Real unew[4];
+    Real draw[4];
+    {
+      const double* ys = reinterpret_cast<const double*>(sb + L.y_off);
+      const Delta* ds = reinterpret_cast<const Delta*>(sb + L.din_off);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int e = (s * 4 + q) * nv + vj;
+        const double yv = active ? ys[e] : 0.0;
+        const Delta dd = (STAGE > 1 && active) ? ds[e] : Delta(0);
+        draw[q] = Real(dd);
+        if (PREC == kFP64)
+          unew[q] = Real(yv + double(dd));
+        else
+          unew[q] = Real(float(yv) + float(dd));
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < WIN - 1; ++k)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) u[k][q] = u[k + 1][q];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) u[WIN - 1][q] = unew[q];
+    if (PREC == kMIXED && STAGE == 4) {
+#pragma unroll
+      for (int k = 0; k < LAG; ++k)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dring[k][q] = dring[k + 1][q];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) dring[LAG][q] = draw[q];
+    }
+
+    // moment contributions of row i (needed when it becomes the center)
+    const int ms_i = (int)(((i % kMomSlots) + kMomSlots) % kMomSlots);
+    if (in_center_range_i && (PREC == kFP64 || STAGE > 1)) {
+      const Real* src = (PREC == kFP64) ? unew : draw;
+      const Real t3 = src[0] - src[1];
+      const Real m6[6] = {w3 * t3, w3v * t3, w3 * src[2], w3v * src[2], wi * src[3], wiv * src[3]};
+      const Real tot = warp_sum6_transposed(m6);
+      const int k = (lane >> 2) & 7;
+      if ((lane & 3) == 0 && k < 6) part[(ms_i * kMaxWarps + warp) * 8 + k] = double(tot);
+    }
+    double my_i = 0.0;  // mixed: running FP64 moment k = lane of row i (warp 0, lanes 0..5)
+    if (PREC == kMIXED && warp == 0 && lane < 6 && in_center_range_i) {
+      my_i = reinterpret_cast<const double*>(sb + L.my_off)[lane];
+    }
+
+    // ---- center row c = i - lag
+    const int64_t c = i - LAG;
+    Real fcur[4] = {Real(0), Real(0), Real(0), Real(0)};
+    if (SCHEME == kWENO7 && c >= z_begin - 1 && c < z_end) {
+      // flux F_{c+1/2} = v * WENO(u), upwind by the sign of v
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        Real r;
+        if (upwind_left)
+          r = weno7_face(u[0][q], u[1][q], u[2][q], u[3][q], u[4][q], u[5][q], u[6][q], eps_v);
+        else
+          r = weno7_face(u[7][q], u[6][q], u[5][q], u[4][q], u[3][q], u[2][q], u[1][q], eps_v);
+        fcur[q] = v * r;
+      }
+    }
+    if (c >= z_begin && c < z_end) {
+      const int ms_c = (int)(((c % kMomSlots) + kMomSlots) % kMomSlots);
+      const double* mf = momf + ms_c * 8;
+      const Real D30 = Real(mf[0]), D31 = Real(mf[1]), Dr0 = Real(mf[2]), Dr1 = Real(mf[3]),
+                 Di0 = Real(mf[4]), Di1 = Real(mf[5]);
+      const Real dH = hd0 + mus * (D30 - v * D31);
+      const Real hr = hr0 + mus * (Dr0 - v * Dr1);
+      const Real hi = mu * (Di0 - v * Di1);
+      constexpr int CC = (SCHEME == kFDKO) ? 2 : 3;  // center index in the window
+      const Real ua = u[CC][0], ub = u[CC][1], ucr = u[CC][2], uci = u[CC][3];
+      const Real amb = ua - ub;
+      Real kk[4];
+      // -i [H, rho] for 2x2 Hermitian matrices, Eq. (eom)
+      const Real adot = Real(2) * (hi * ucr - hr * uci);
+      kk[0] = adot;
+      kk[1] = -adot;
+      kk[2] = dH * uci - amb * hi;
+      kk[3] = -dH * ucr + amb * hr;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        Real adv;
+        if (SCHEME == kFDKO) {
+          const Real um2 = u[0][q], um1 = u[1][q], u0 = u[2][q], up1 = u[3][q], up2 = u[4][q];
+          const Real fd = Real(8) * (up1 - um1) - (up2 - um2);
+          const Real ko = (um2 + up2) - Real(4) * (um1 + up1) + Real(6) * u0;
+          adv = c_fd * fd + c_ko * ko;
+        } else {
+          adv = -(fcur[q] - fprev[q]) * inv_dz;
+        }
+        kk[q] += adv;
+      }
+      Delta* dout = static_cast<Delta*>(a.d_out);
+      if (STAGE < 4) {
+        const Real f = (STAGE == 3) ? dt : Real(0.5) * dt;
+        if (active) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q)
+            dout[((int64_t)(s * 4 + q) * nz + c) * nv + vj] = Delta(f * kk[q]);
+        }
+      } else {
+        const double* yc = reinterpret_cast<const double*>(sb + L.yc_off);
+        const Delta* d1c = reinterpret_cast<const Delta*>(sb + L.d1c_off);
+        const Delta* d2c = reinterpret_cast<const Delta*>(sb + L.d2c_off);
+        Real incr[4];
+        bool bad = false;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int e = (s * 4 + q) * nv + vj;
+          const double y0 = active ? yc[e] : 0.0;
+          const Real e1 = active ? Real(d1c[e]) : Real(0);
+          const Real e2 = active ? Real(d2c[e]) : Real(0);
+          Real e3;
+          if (PREC == kFP64)
+            e3 = Real(double(u[CC][q]) - y0);  // u = y + delta_3 at the center
+          else
+            e3 = dring[0][q];
+          incr[q] = (e1 + Real(2) * e2 + e3) * Real(1.0 / 3.0) + (dt * Real(1.0 / 6.0)) * kk[q];
+          const double ynew = y0 + double(incr[q]);
+          bad |= !is_finite_bits(ynew);
+          if (active) a.y_out[((int64_t)(s * 4 + q) * nz + c) * nv + vj] = ynew;
+        }
+        nonfinite |= bad;
+        if (PREC == kMIXED) {
+          // float moments of the increment: advance the FP64 running moments of y
+          const Real t3 = incr[0] - incr[1];
+          const Real m6[6] = {w3 * t3, w3v * t3, w3 * incr[2], w3v * incr[2], wi * incr[3],
+                              wiv * incr[3]};
+          const Real tot = warp_sum6_transposed(m6);
+          const int k = (lane >> 2) & 7;
+          if ((lane & 3) == 0 && k < 6) partdy[(ms_c * kMaxWarps + warp) * 8 + k] = double(tot);
+        }
+      }
+    }
+    if (SCHEME == kWENO7) {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) fprev[q] = fcur[q];
+    }
+
+    __syncthreads();  // (A) slot j and the partials of rows i and c are complete
+    if (flags[0]) {  // a bounded wait gave up somewhere in the CTA
+      jbreak = j;
+      break;
+    }
+
+    if (tid == 0 && j + D < nrows) {
+      fence_proxy_async();
+      issue_row(j + D);
+    }
+    if (warp == 0 && lane < 6 && in_center_range_i) {
+      // finish the moments of row i (used when i is the center, lag iterations later)
+      double acc = 0.0;
+      if (PREC == kFP64 || STAGE > 1) {
+        for (int w = 0; w < nwarps; ++w) acc += part[(ms_i * kMaxWarps + w) * 8 + lane];
+      }
+      if (PREC == kMIXED) {
+        myring[ms_i * 8 + lane] = my_i;
+        acc = my_i + acc;
+        momf[ms_i * 8 + lane] = double(float(acc));
+      } else {
+        momf[ms_i * 8 + lane] = acc;
+      }
+    }
+    if (PREC == kMIXED && STAGE == 4 && warp == 0 && lane >= 8 && lane < 14 && c >= z_begin &&
+        c < z_end) {
+      const int k = lane - 8;
+      const int ms_c = (int)(((c % kMomSlots) + kMomSlots) % kMomSlots);
+      double acc = 0.0;
+      for (int w = 0; w < nwarps; ++w) acc += partdy[(ms_c * kMaxWarps + w) * 8 + k];
+      a.my[c * 8 + k] = myring[ms_c * 8 + k] + acc;
+    }
+  }
+
+  if (STAGE == 4) {
+    const unsigned any = __ballot_sync(0xffffffffu, nonfinite);
+    if (lane == 0 && any) atomicOr(a.err, kErrNonFinite);
+  }
+  if (jbreak >= 0 && tid == 0) {
+    // Leave only after the copies this CTA issued and did not consume have
+    // landed (each wait bounded): rows jbreak .. min(nrows, jbreak + D) - 1.
+    const int64_t jend = (jbreak + (int64_t)D) < nrows ? (jbreak + (int64_t)D) : nrows;
+    for (int64_t jj = jbreak; jj < jend; ++jj)
+      mbar_wait_bounded(bar0 + 8 * (uint32_t)(jj % D), (uint32_t)((jj / D) & 1));
+  }
+}
+
+}  // namespace cosenu

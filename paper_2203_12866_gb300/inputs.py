@@ -85,3 +85,42 @@ def single_mode_state(nz: int, nv: int, k_index: int, *, alpha=0.9, sigma_nu=0.6
     s[0, 2] = (eps0 * np.cos(ph))[:, None]
     s[0, 3] = (eps0 * np.sin(ph))[:, None]
     return s
+
+
+def collective_rows(z_index: np.ndarray, nv: int, *, alpha=0.9, sigma_nu=0.6, sigma_nubar=0.5,
+                    eps0=1e-6, seed=12866) -> np.ndarray:
+    """Rows z_index (any integers, taken as given) of collective_state(): the same
+    values without building the whole grid.  Shape [2][4][len(z_index)][nv]."""
+    z_index = np.asarray(z_index, dtype=np.int64)
+    g = angular_gaussian(nv, sigma_nu)
+    gb = angular_gaussian(nv, sigma_nubar)
+    n = int(z_index.max()) + 1 if z_index.size else 0
+    phi = 2.0 * np.pi * uniform01(n, seed)[z_index]
+    s = np.zeros((2, 4, z_index.size, nv))
+    s[0, 0] = g[None, :]
+    s[1, 0] = alpha * gb[None, :]
+    for sp in range(2):
+        s[sp, 2] = (eps0 * np.cos(phi))[:, None]
+        s[sp, 3] = (eps0 * np.sin(phi))[:, None]
+    return s
+
+
+def collective_state_device(nz: int, nv: int, device, *, alpha=0.9, sigma_nu=0.6,
+                            sigma_nubar=0.5, eps0=1e-6, seed=12866):
+    """collective_state() built on a torch device from the same host-computed
+    vectors (g(v), eps0 cos phi(z), eps0 sin phi(z)); the device only broadcasts,
+    so the values are bit-identical to the host version."""
+    import torch
+
+    g = torch.from_numpy(angular_gaussian(nv, sigma_nu)).to(device)
+    gb = torch.from_numpy(alpha * angular_gaussian(nv, sigma_nubar)).to(device)
+    phi = 2.0 * np.pi * uniform01(nz, seed)
+    cr = torch.from_numpy(eps0 * np.cos(phi)).to(device)
+    ci = torch.from_numpy(eps0 * np.sin(phi)).to(device)
+    s = torch.zeros((2, 4, nz, nv), dtype=torch.float64, device=device)
+    s[0, 0] = g[None, :]
+    s[1, 0] = gb[None, :]
+    for sp in range(2):
+        s[sp, 2] = cr[:, None]
+        s[sp, 3] = ci[:, None]
+    return s
