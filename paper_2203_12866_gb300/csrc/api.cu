@@ -154,10 +154,10 @@ int configure(cosenu_t h) {
                                                  : stage_smem_header_bytes<kMIXED>();
   for (int s = 1; s <= 4; ++s) {
     StageCfg c;
-    c.block = ((2 * h->nv + 31) / 32) * 32;
+    c.block = ((2 * h->nv + 31) / 32) * 32 + 64;  // consumers + producer + reducer warps
     c.slot_bytes = slot_bytes(h, s);
     int best_occ = 0, best_d = 0;
-    for (int D = 2; D <= 8; ++D) {
+    for (int D = 2; D <= kMaxRing; ++D) {
       const size_t smem = (size_t)header + (size_t)D * c.slot_bytes;
       if (smem > (size_t)kSmemLimit) break;
       const int occ = max_blocks(h, s, c.block, smem);

@@ -20,9 +20,13 @@ constexpr uint32_t kErrTimeout = 2u;
 // A bounded wait gives up after this many SM clock cycles (about 2 s).
 constexpr long long kWaitLimitCycles = 4000000000LL;
 
-// Ring of moment slots per CTA; must exceed the stencil lag (2 or 4 rows).
-constexpr int kMomSlots = 8;
-constexpr int kMaxWarps = 16;  // 2 * nv / 32 with nv <= 256
+// Ring of moment slots per CTA.  Consumer warps drift apart by at most the
+// bulk-copy ring depth (kMaxRing rows), so a slot is reused only after
+// kMomSlots > lag + kMaxRing rows.
+constexpr int kMomSlots = 16;
+constexpr int kMaxRing = 8;
+constexpr int kMaxWarps = 16;  // consumer warps: 2 * nv / 32 with nv <= 256
+constexpr int kMaxThreads = (kMaxWarps + 2) * 32;  // + producer and reducer warps
 
 // Arguments of one RK4 stage launch.  All arrays use the layout
 // [8 = species*4 + component][nz][nv]; Delta is double (FP64) or float (mixed).
@@ -74,6 +78,10 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t byt
                : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -94,6 +102,23 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
     if (clock64() - t0 > kWaitLimitCycles) return false;
   }
   return true;
+}
+
+// Same, but also returns false as soon as another warp of the CTA has raised
+// the abort flag; raises it (and the device error bit) on its own timeout.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint32_t bar, uint32_t parity,
+                                                   volatile int* abort_flag, uint32_t* err) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  for (uint32_t it = 0;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 63) == 0 && *abort_flag) return false;
+    if (clock64() - t0 > kWaitLimitCycles) {
+      *abort_flag = 1;
+      atomicOr(err, kErrTimeout);
+      return false;
+    }
+  }
 }
 
 // Bulk copy (TMA, non-tensor) of `bytes` from global to this CTA's shared

@@ -8,15 +8,20 @@
 //   y <- y + (delta_1 + 2 delta_2 + delta_3) / 3 + dt/6 k_4   (classic RK4)
 //
 // Work decomposition.  A CTA owns a contiguous range of z rows and all 2 nv
-// (species, v) columns; thread t is column t.  The CTA marches along z: each
-// iteration one new row enters (bulk-copied by the TMA into a ring of shared
-// memory slots, several rows ahead), every thread keeps a sliding window of
-// its column in registers, and the row `lag` behind the leading one is
-// finished.  Because the CTA holds every v of a row, the velocity moments that
-// form H_nunu are reduced inside the CTA (warp shuffles, then a cross-warp sum
-// in shared memory) while the row waits to become the center.  Each stage
-// therefore reads the state once from HBM (plus a 2 x lag row halo per CTA)
-// and writes its output once.
+// (species, v) columns, and marches along z with three warp roles:
+//  - consumer warps (one thread per column): each iteration one new row
+//    enters the thread's sliding register window and the row `lag` behind it
+//    is finished (Hamiltonian, commutator, stencil, RK update, store);
+//  - a producer warp: one lane bulk-copies rows (TMA, cp.async.bulk) into a
+//    ring of shared-memory slots up to `ring` rows ahead (full / empty
+//    mbarrier pairs);
+//  - a reducer warp: sums the consumers' per-warp partial velocity moments of
+//    each row and publishes the row's moments through an mbarrier.
+// Consumer warps never meet at a CTA-wide barrier: a row's moments are
+// produced while the row waits `lag` iterations to become the center, so the
+// mbarrier waits are normally already satisfied.  Because the CTA holds every
+// v of a row, the moments need no cross-CTA step.  Each stage reads the state
+// once from HBM (plus a 2 x lag row halo per CTA) and writes its output once.
 //
 // Moments.  H_nunu(v) = mu sum_j dv (1 - v v_j) [S_j - Sbar_j^*] is separable:
 // with D_n = sum_j dv v_j^n (S_j - Sbar_j^*), H_nunu(v) = mu (D_0 - v D_1).
@@ -89,12 +94,28 @@ __host__ __device__ inline SlotLayout slot_layout(int nv, int stage) {
   return L;
 }
 
-// Shared memory besides the ring: mbarriers, moment partials, finished moments.
+// Shared memory besides the ring.  Acc is the type of the moment partials.
+//   mbarriers: full[kMaxRing] empty[kMaxRing] part[kMomSlots] mom[kMomSlots] dy[kMomSlots]
+//   flags (abort), partials [kMomSlots][kMaxWarps][8] Acc, dy partials (mixed
+//   only, same shape), finished moments [kMomSlots][8] Acc, running moments of
+//   y (mixed) [kMomSlots][8] double.
+template <int PREC>
+struct SmemHeader {
+  using Acc = typename Prec<PREC>::Real;
+  static constexpr int kBars = 0;
+  static constexpr int kNumBars = 2 * kMaxRing + 3 * kMomSlots;
+  static constexpr int kFlags = kBars + kNumBars * 8;
+  static constexpr int kPart = ((kFlags + 64) + 127) & ~127;
+  static constexpr int kPartBytes = kMomSlots * kMaxWarps * 8 * (int)sizeof(Acc);
+  static constexpr int kPartDy = kPart + kPartBytes;
+  static constexpr int kMomf = kPartDy + (PREC == kMIXED ? kPartBytes : 0);
+  static constexpr int kMyRing = kMomf + kMomSlots * 8 * (int)sizeof(Acc);
+  static constexpr int kBytes = ((kMyRing + kMomSlots * 8 * 8) + 127) & ~127;
+};
+
 template <int PREC>
 __host__ __device__ inline int stage_smem_header_bytes() {
-  // mbarriers (16 x 8) | part[kMomSlots][kMaxWarps][8] double | partdy (same) |
-  // momf[kMomSlots][8] double | myring[kMomSlots][8] double | flags
-  return 128 + 2 * kMomSlots * kMaxWarps * 8 * 8 + 2 * kMomSlots * 8 * 8 + 128;
+  return SmemHeader<PREC>::kBytes;
 }
 
 __device__ __forceinline__ int64_t wrap_row(int64_t r, int64_t nz) {
@@ -172,39 +193,152 @@ __device__ __forceinline__ float weno7_face(float fm3, float fm2, float fm1, flo
 // ---------------------------------------------------------------- the kernel
 
 template <int SCHEME, int PREC, int STAGE>
-__global__ void __launch_bounds__(512, 1) rk4_stage_kernel(const StageArgs a) {
+__global__ void __launch_bounds__(kMaxThreads) rk4_stage_kernel(const StageArgs a) {
   using Real = typename Prec<PREC>::Real;
   using Delta = typename Prec<PREC>::Delta;
+  using Acc = Real;
+  using H = SmemHeader<PREC>;
   constexpr int LAG = Scheme<SCHEME>::kLag;
   constexpr int WIN = Scheme<SCHEME>::kWin;
   constexpr int LO = Scheme<SCHEME>::kLo;
   constexpr int HI = Scheme<SCHEME>::kHi;
+  constexpr int MS = kMomSlots;
 
   extern __shared__ __align__(128) unsigned char smem[];
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem);                           // [16]
-  double* part = reinterpret_cast<double*>(smem + 128);                         // [MS][W][8]
-  double* partdy = part + kMomSlots * kMaxWarps * 8;                            // [MS][W][8]
-  double* momf = partdy + kMomSlots * kMaxWarps * 8;                            // [MS][8]
-  double* myring = momf + kMomSlots * 8;                                        // [MS][8]
-  int* flags = reinterpret_cast<int*>(myring + kMomSlots * 8);                  // [32]
-  unsigned char* ring = smem + stage_smem_header_bytes<PREC>();
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + H::kFlags);
+  Acc* part = reinterpret_cast<Acc*>(smem + H::kPart);      // [MS][kMaxWarps][8]
+  Acc* partdy = reinterpret_cast<Acc*>(smem + H::kPartDy);  // [MS][kMaxWarps][8]
+  Acc* momf = reinterpret_cast<Acc*>(smem + H::kMomf);      // [MS][8]
+  double* myring = reinterpret_cast<double*>(smem + H::kMyRing);  // [MS][8]
+  unsigned char* ring = smem + H::kBytes;
 
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int warp = tid >> 5;
-  const int nwarps = blockDim.x >> 5;
+  const int ncw = (a.ncols + 31) >> 5;  // consumer warps; then producer, reducer
   const int64_t nz = a.nz;
   const int nv = a.nv;
   const SlotLayout L = slot_layout<PREC>(nv, STAGE);
+  const int D = a.ring;
 
   const int64_t z_begin = (int64_t)blockIdx.x * a.rows_per_cta;
   const int64_t z_end = min(nz, z_begin + a.rows_per_cta);
   if (z_begin >= z_end) return;  // uniform over the CTA
   const int64_t i_first = z_begin - LO;
   const int64_t nrows = (z_end + HI) - i_first;
-  const int D = a.ring;
+  const int64_t ncent = z_end - z_begin;
 
-  // ---- per-column constants
+  const uint32_t bar0 = smem_addr(smem + H::kBars);
+  auto full_bar = [&](int k) { return bar0 + 8u * k; };
+  auto empty_bar = [&](int k) { return bar0 + 8u * (kMaxRing + k); };
+  auto part_bar = [&](int m) { return bar0 + 8u * (2 * kMaxRing + m); };
+  auto mom_bar = [&](int m) { return bar0 + 8u * (2 * kMaxRing + MS + m); };
+  auto dy_bar = [&](int m) { return bar0 + 8u * (2 * kMaxRing + 2 * MS + m); };
+
+  // Every lane waits (so each observes the phase), and the warp leaves together.
+  auto warp_wait = [&](uint32_t bar, uint32_t parity) {
+    const bool ok = mbar_wait_or_abort(bar, parity, abort_flag, a.err);
+    return __all_sync(0xffffffffu, ok);
+  };
+
+  if (tid == 0) {
+    for (int k = 0; k < kMaxRing; ++k) {
+      mbar_init(full_bar(k), 1);
+      mbar_init(empty_bar(k), ncw);
+    }
+    for (int m = 0; m < MS; ++m) {
+      mbar_init(part_bar(m), ncw);
+      mbar_init(mom_bar(m), 1);
+      mbar_init(dy_bar(m), ncw);
+    }
+    *abort_flag = 0;
+    fence_barrier_init();
+  }
+  __syncthreads();  // the only CTA-wide barrier
+
+  // =================================================================== producer
+  if (warp == ncw) {
+    if (lane != 0) return;
+    const uint32_t ry = nv * sizeof(double), rd = nv * sizeof(Delta);
+    const Delta* din = static_cast<const Delta*>(a.d_in);
+    const Delta* d1 = static_cast<const Delta*>(a.d1);
+    const Delta* d2 = static_cast<const Delta*>(a.d2);
+    int64_t issued = 0;
+    for (int64_t j = 0; j < nrows; ++j) {
+      const int slot = (int)(j % D);
+      const int64_t n = j / D;
+      if (n > 0 && !mbar_wait_or_abort(empty_bar(slot), (uint32_t)((n - 1) & 1), abort_flag, a.err))
+        break;
+      fence_proxy_async();
+      const uint32_t bar = full_bar(slot);
+      const uint32_t base = smem_addr(ring + (size_t)slot * a.slot_bytes);
+      const int64_t i = i_first + j;
+      const int64_t r = wrap_row(i, nz);
+      const int64_t c = i - LAG;
+      const bool has_center = (STAGE == 4) && c >= z_begin && c < z_end;
+      const bool has_my = (PREC == kMIXED) && i >= z_begin && i < z_end;
+      uint32_t tx = 8 * ry + (STAGE > 1 ? 8 * rd : 0);
+      if (has_center) tx += 8 * ry + 16 * rd;
+      if (has_my) tx += 64;
+      mbar_arrive_expect_tx(bar, tx);
+      const int64_t plane = nz * nv;
+      const double* ysrc = a.y_in + r * nv;
+#pragma unroll 1
+      for (int q = 0; q < 8; ++q) {
+        bulk_g2s(base + L.y_off + q * ry, ysrc + q * plane, ry, bar);
+        if (STAGE > 1) bulk_g2s(base + L.din_off + q * rd, din + r * nv + q * plane, rd, bar);
+      }
+      if (has_center) {
+#pragma unroll 1
+        for (int q = 0; q < 8; ++q) {
+          const int64_t o = q * plane + c * nv;
+          bulk_g2s(base + L.yc_off + q * ry, a.y_in + o, ry, bar);
+          bulk_g2s(base + L.d1c_off + q * rd, d1 + o, rd, bar);
+          bulk_g2s(base + L.d2c_off + q * rd, d2 + o, rd, bar);
+        }
+      }
+      if (has_my) bulk_g2s(base + L.my_off, a.my + i * 8, 64, bar);
+      issued = j + 1;
+    }
+    // Leave only after the last fill of every slot has landed (each wait bounded).
+    for (int64_t j = (issued > D ? issued - D : 0); j < issued; ++j)
+      mbar_wait_bounded(full_bar((int)(j % D)), (uint32_t)((j / D) & 1));
+    return;
+  }
+
+  // =================================================================== reducer
+  if (warp == ncw + 1) {
+    auto finish_dy = [&](int64_t rc) {  // mixed stage 4: advance the running moments of y
+      const int m = (int)(rc % MS);
+      if (!warp_wait(dy_bar(m), (uint32_t)((rc / MS) & 1))) return false;
+      if (lane < 6) {
+        Acc acc = Acc(0);
+        for (int w = 0; w < ncw; ++w) acc += partdy[(m * kMaxWarps + w) * 8 + lane];
+        a.my[(z_begin + rc) * 8 + lane] = myring[m * 8 + lane] + double(acc);
+      }
+      return true;
+    };
+    for (int64_t rc = 0; rc < ncent; ++rc) {
+      const int m = (int)(rc % MS);
+      if (!warp_wait(part_bar(m), (uint32_t)((rc / MS) & 1))) return;
+      if (lane < 6) {
+        Acc acc = Acc(0);
+        if (PREC == kFP64 || STAGE > 1)
+          for (int w = 0; w < ncw; ++w) acc += part[(m * kMaxWarps + w) * 8 + lane];
+        if (PREC == kMIXED)
+          momf[m * 8 + lane] = Acc(myring[m * 8 + lane] + double(acc));
+        else
+          momf[m * 8 + lane] = acc;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(mom_bar(m));
+      if (PREC == kMIXED && STAGE == 4 && rc > 0 && !finish_dy(rc - 1)) return;
+    }
+    if (PREC == kMIXED && STAGE == 4 && ncent > 0) finish_dy(ncent - 1);
+    return;
+  }
+
+  // =================================================================== consumers
   const bool active = tid < a.ncols;
   const int s = active ? tid / nv : 0;  // species
   const int vj = active ? tid % nv : 0;
@@ -223,65 +357,15 @@ __global__ void __launch_bounds__(512, 1) rk4_stage_kernel(const StageArgs a) {
   const Real hr0 = Real(a.hvac_r);
   const Real mus = Real(sgn * a.mu);
   const Real mu = Real(a.mu);
-  // advection coefficients
   const Real c_fd = Real(-vd * a.inv_dz / 12.0);
   const Real c_ko = Real(-a.ko_eps * a.inv_dz / 16.0);
   const Real inv_dz = Real(a.inv_dz);
   const Real eps_v = Real(a.weno_eps / (vd * vd));  // WENO_eps(v u) = v WENO_{eps/v^2}(u)
   const bool upwind_left = vd > 0.0;
   const Real dt = Real(a.dt);
-  const double dt_d = a.dt;
+  const int64_t plane = nz * nv;
+  const int ecol = s * 4 * nv + vj;  // element of component 0 in a slot row
 
-  // ---- barriers and prologue copies
-  const uint32_t bar0 = smem_addr(bars);
-  if (tid == 0) {
-    for (int k = 0; k < D; ++k) mbar_init(bar0 + 8 * k, 1);
-    flags[0] = 0;
-    fence_barrier_init();
-  }
-  __syncthreads();
-
-  // Issue the copies of relative row j into its slot (producer thread only).
-  auto issue_row = [&](int64_t j) {
-    const int slot = (int)(j % D);
-    const uint32_t bar = bar0 + 8 * slot;
-    const uint32_t base = smem_addr(ring + (size_t)slot * a.slot_bytes);
-    const int64_t i = i_first + j;
-    const int64_t r = wrap_row(i, nz);
-    const int64_t c = i - LAG;
-    const bool has_center = (STAGE == 4) && c >= z_begin && c < z_end;
-    const bool has_my = (PREC == kMIXED) && i >= z_begin && i < z_end;
-    const uint32_t ry = nv * sizeof(double), rd = nv * sizeof(Delta);
-    uint32_t tx = 8 * ry + (STAGE > 1 ? 8 * rd : 0);
-    if (has_center) tx += 8 * ry + 16 * rd;
-    if (has_my) tx += 64;
-    mbar_arrive_expect_tx(bar, tx);
-    const Delta* din = static_cast<const Delta*>(a.d_in);
-#pragma unroll 1
-    for (int q = 0; q < 8; ++q) {
-      bulk_g2s(base + L.y_off + q * ry, a.y_in + ((int64_t)q * nz + r) * nv, ry, bar);
-      if (STAGE > 1) bulk_g2s(base + L.din_off + q * rd, din + ((int64_t)q * nz + r) * nv, rd, bar);
-    }
-    if (has_center) {
-      const Delta* d1 = static_cast<const Delta*>(a.d1);
-      const Delta* d2 = static_cast<const Delta*>(a.d2);
-#pragma unroll 1
-      for (int q = 0; q < 8; ++q) {
-        const int64_t o = ((int64_t)q * nz + c) * nv;
-        bulk_g2s(base + L.yc_off + q * ry, a.y_in + o, ry, bar);
-        bulk_g2s(base + L.d1c_off + q * rd, d1 + o, rd, bar);
-        bulk_g2s(base + L.d2c_off + q * rd, d2 + o, rd, bar);
-      }
-    }
-    if (has_my) bulk_g2s(base + L.my_off, a.my + i * 8, 64, bar);
-  };
-
-  if (tid == 0) {
-    const int64_t npro = nrows < (int64_t)D ? nrows : (int64_t)D;
-    for (int64_t j = 0; j < npro; ++j) issue_row(j);
-  }
-
-  // ---- per-thread window
   Real u[WIN][4];
 #pragma unroll
   for (int k = 0; k < WIN; ++k)
@@ -293,32 +377,29 @@ __global__ void __launch_bounds__(512, 1) rk4_stage_kernel(const StageArgs a) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) dring[k][q] = Real(0);
   Real fprev[4] = {Real(0), Real(0), Real(0), Real(0)};  // WENO flux at c - 1/2
-  bool ok = true;
   bool nonfinite = false;
-  int64_t jbreak = -1;
 
 #pragma unroll 1
   for (int64_t j = 0; j < nrows; ++j) {
     const int64_t i = i_first + j;
     const int slot = (int)(j % D);
     const unsigned char* sb = ring + (size_t)slot * a.slot_bytes;
-    const bool in_center_range_i = i >= z_begin && i < z_end;
+    const int64_t c = i - LAG;
+    const bool lead_in_range = i >= z_begin && i < z_end;
+    const bool center_in_range = c >= z_begin && c < z_end;
 
-    if (ok && !mbar_wait_bounded(bar0 + 8 * slot, (uint32_t)((j / D) & 1))) {
-      ok = false;
-      atomicOr(a.err, kErrTimeout);
-      flags[0] = 1;
-    }
+    if (!warp_wait(full_bar(slot), (uint32_t)((j / D) & 1))) break;
 
-    // ---- leading row i enters the window
-    Real unew[4];
-    Real draw[4];
+    // ---- read the slot: leading row i (window arrays), center row c (stage 4)
+    Real unew[4], draw[4];
+    double yc[4];
+    Real e1[4], e2[4];
     {
       const double* ys = reinterpret_cast<const double*>(sb + L.y_off);
       const Delta* ds = reinterpret_cast<const Delta*>(sb + L.din_off);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int e = (s * 4 + q) * nv + vj;
+        const int e = ecol + q * nv;
         const double yv = active ? ys[e] : 0.0;
         const Delta dd = (STAGE > 1 && active) ? ds[e] : Delta(0);
         draw[q] = Real(dd);
@@ -327,7 +408,25 @@ __global__ void __launch_bounds__(512, 1) rk4_stage_kernel(const StageArgs a) {
         else
           unew[q] = Real(float(yv) + float(dd));
       }
+      if (STAGE == 4 && center_in_range) {
+        const double* ycs = reinterpret_cast<const double*>(sb + L.yc_off);
+        const Delta* d1s = reinterpret_cast<const Delta*>(sb + L.d1c_off);
+        const Delta* d2s = reinterpret_cast<const Delta*>(sb + L.d2c_off);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int e = ecol + q * nv;
+          yc[q] = active ? ycs[e] : 0.0;
+          e1[q] = active ? Real(d1s[e]) : Real(0);
+          e2[q] = active ? Real(d2s[e]) : Real(0);
+        }
+      }
+      if (PREC == kMIXED && warp == 0 && lane < 6 && lead_in_range)
+        myring[(int)((i - z_begin) % MS) * 8 + lane] =
+            reinterpret_cast<const double*>(sb + L.my_off)[lane];
     }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(empty_bar(slot));
+
 #pragma unroll
     for (int k = 0; k < WIN - 1; ++k)
 #pragma unroll
@@ -343,23 +442,23 @@ __global__ void __launch_bounds__(512, 1) rk4_stage_kernel(const StageArgs a) {
       for (int q = 0; q < 4; ++q) dring[LAG][q] = draw[q];
     }
 
-    // moment contributions of row i (needed when it becomes the center)
-    const int ms_i = (int)(((i % kMomSlots) + kMomSlots) % kMomSlots);
-    if (in_center_range_i && (PREC == kFP64 || STAGE > 1)) {
-      const Real* src = (PREC == kFP64) ? unew : draw;
-      const Real t3 = src[0] - src[1];
-      const Real m6[6] = {w3 * t3, w3v * t3, w3 * src[2], w3v * src[2], wi * src[3], wiv * src[3]};
-      const Real tot = warp_sum6_transposed(m6);
-      const int k = (lane >> 2) & 7;
-      if ((lane & 3) == 0 && k < 6) part[(ms_i * kMaxWarps + warp) * 8 + k] = double(tot);
-    }
-    double my_i = 0.0;  // mixed: running FP64 moment k = lane of row i (warp 0, lanes 0..5)
-    if (PREC == kMIXED && warp == 0 && lane < 6 && in_center_range_i) {
-      my_i = reinterpret_cast<const double*>(sb + L.my_off)[lane];
+    // ---- partial velocity moments of row i (finished by the reducer)
+    if (lead_in_range) {
+      const int m = (int)((i - z_begin) % MS);
+      if (PREC == kFP64 || STAGE > 1) {
+        const Real* src = (PREC == kFP64) ? unew : draw;
+        const Real t3 = src[0] - src[1];
+        const Real m6[6] = {w3 * t3, w3v * t3, w3 * src[2], w3v * src[2], wi * src[3],
+                            wiv * src[3]};
+        const Real tot = warp_sum6_transposed(m6);
+        const int k = (lane >> 2) & 7;
+        if ((lane & 3) == 0 && k < 6) part[(m * kMaxWarps + warp) * 8 + k] = tot;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(part_bar(m));
     }
 
     // ---- center row c = i - lag
-    const int64_t c = i - LAG;
     Real fcur[4] = {Real(0), Real(0), Real(0), Real(0)};
     if (SCHEME == kWENO7 && c >= z_begin - 1 && c < z_end) {
       // flux F_{c+1/2} = v * WENO(u), upwind by the sign of v
@@ -373,9 +472,11 @@ __global__ void __launch_bounds__(512, 1) rk4_stage_kernel(const StageArgs a) {
         fcur[q] = v * r;
       }
     }
-    if (c >= z_begin && c < z_end) {
-      const int ms_c = (int)(((c % kMomSlots) + kMomSlots) % kMomSlots);
-      const double* mf = momf + ms_c * 8;
+    if (center_in_range) {
+      const int64_t rc = c - z_begin;
+      const int m = (int)(rc % MS);
+      if (!warp_wait(mom_bar(m), (uint32_t)((rc / MS) & 1))) break;
+      const Acc* mf = momf + m * 8;
       const Real D30 = Real(mf[0]), D31 = Real(mf[1]), Dr0 = Real(mf[2]), Dr1 = Real(mf[3]),
                  Di0 = Real(mf[4]), Di1 = Real(mf[5]);
       const Real dH = hd0 + mus * (D30 - v * D31);
@@ -404,45 +505,41 @@ __global__ void __launch_bounds__(512, 1) rk4_stage_kernel(const StageArgs a) {
         }
         kk[q] += adv;
       }
-      Delta* dout = static_cast<Delta*>(a.d_out);
+      const int64_t gout = (int64_t)(s * 4) * plane + c * nv + vj;  // component 0, row c
       if (STAGE < 4) {
+        Delta* dout = static_cast<Delta*>(a.d_out);
         const Real f = (STAGE == 3) ? dt : Real(0.5) * dt;
         if (active) {
 #pragma unroll
-          for (int q = 0; q < 4; ++q)
-            dout[((int64_t)(s * 4 + q) * nz + c) * nv + vj] = Delta(f * kk[q]);
+          for (int q = 0; q < 4; ++q) dout[gout + (int64_t)q * plane] = Delta(f * kk[q]);
         }
       } else {
-        const double* yc = reinterpret_cast<const double*>(sb + L.yc_off);
-        const Delta* d1c = reinterpret_cast<const Delta*>(sb + L.d1c_off);
-        const Delta* d2c = reinterpret_cast<const Delta*>(sb + L.d2c_off);
         Real incr[4];
         bool bad = false;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const int e = (s * 4 + q) * nv + vj;
-          const double y0 = active ? yc[e] : 0.0;
-          const Real e1 = active ? Real(d1c[e]) : Real(0);
-          const Real e2 = active ? Real(d2c[e]) : Real(0);
           Real e3;
           if (PREC == kFP64)
-            e3 = Real(double(u[CC][q]) - y0);  // u = y + delta_3 at the center
+            e3 = Real(double(u[CC][q]) - yc[q]);  // u = y + delta_3 at the center
           else
             e3 = dring[0][q];
-          incr[q] = (e1 + Real(2) * e2 + e3) * Real(1.0 / 3.0) + (dt * Real(1.0 / 6.0)) * kk[q];
-          const double ynew = y0 + double(incr[q]);
+          incr[q] = (e1[q] + Real(2) * e2[q] + e3) * Real(1.0 / 3.0) +
+                    (dt * Real(1.0 / 6.0)) * kk[q];
+          const double ynew = yc[q] + double(incr[q]);
           bad |= !is_finite_bits(ynew);
-          if (active) a.y_out[((int64_t)(s * 4 + q) * nz + c) * nv + vj] = ynew;
+          if (active) a.y_out[gout + (int64_t)q * plane] = ynew;
         }
         nonfinite |= bad;
         if (PREC == kMIXED) {
-          // float moments of the increment: advance the FP64 running moments of y
+          // float moments of the increment advance the FP64 running moments of y
           const Real t3 = incr[0] - incr[1];
           const Real m6[6] = {w3 * t3, w3v * t3, w3 * incr[2], w3v * incr[2], wi * incr[3],
                               wiv * incr[3]};
           const Real tot = warp_sum6_transposed(m6);
           const int k = (lane >> 2) & 7;
-          if ((lane & 3) == 0 && k < 6) partdy[(ms_c * kMaxWarps + warp) * 8 + k] = double(tot);
+          if ((lane & 3) == 0 && k < 6) partdy[(m * kMaxWarps + warp) * 8 + k] = tot;
+          __syncwarp();
+          if (lane == 0) mbar_arrive(dy_bar(m));
         }
       }
     }
@@ -450,51 +547,11 @@ __global__ void __launch_bounds__(512, 1) rk4_stage_kernel(const StageArgs a) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) fprev[q] = fcur[q];
     }
-
-    __syncthreads();  // (A) slot j and the partials of rows i and c are complete
-    if (flags[0]) {  // a bounded wait gave up somewhere in the CTA
-      jbreak = j;
-      break;
-    }
-
-    if (tid == 0 && j + D < nrows) {
-      fence_proxy_async();
-      issue_row(j + D);
-    }
-    if (warp == 0 && lane < 6 && in_center_range_i) {
-      // finish the moments of row i (used when i is the center, lag iterations later)
-      double acc = 0.0;
-      if (PREC == kFP64 || STAGE > 1) {
-        for (int w = 0; w < nwarps; ++w) acc += part[(ms_i * kMaxWarps + w) * 8 + lane];
-      }
-      if (PREC == kMIXED) {
-        myring[ms_i * 8 + lane] = my_i;
-        acc = my_i + acc;
-        momf[ms_i * 8 + lane] = double(float(acc));
-      } else {
-        momf[ms_i * 8 + lane] = acc;
-      }
-    }
-    if (PREC == kMIXED && STAGE == 4 && warp == 0 && lane >= 8 && lane < 14 && c >= z_begin &&
-        c < z_end) {
-      const int k = lane - 8;
-      const int ms_c = (int)(((c % kMomSlots) + kMomSlots) % kMomSlots);
-      double acc = 0.0;
-      for (int w = 0; w < nwarps; ++w) acc += partdy[(ms_c * kMaxWarps + w) * 8 + k];
-      a.my[c * 8 + k] = myring[ms_c * 8 + k] + acc;
-    }
   }
 
   if (STAGE == 4) {
     const unsigned any = __ballot_sync(0xffffffffu, nonfinite);
     if (lane == 0 && any) atomicOr(a.err, kErrNonFinite);
-  }
-  if (jbreak >= 0 && tid == 0) {
-    // Leave only after the copies this CTA issued and did not consume have
-    // landed (each wait bounded): rows jbreak .. min(nrows, jbreak + D) - 1.
-    const int64_t jend = (jbreak + (int64_t)D) < nrows ? (jbreak + (int64_t)D) : nrows;
-    for (int64_t jj = jbreak; jj < jend; ++jj)
-      mbar_wait_bounded(bar0 + 8 * (uint32_t)(jj % D), (uint32_t)((jj / D) & 1));
   }
 }
 
