@@ -38,15 +38,19 @@ sys.path.insert(0, ROOT)
 NZ, NV = 1 << 20, 256
 DZ = 3200.0 / 65536.0
 L = NZ * DZ
+NZ_FULL = NZ
 MU, ALPHA, SIG_NU, SIG_NUBAR, EPS0, SEED = 10.0, 0.9, 0.6, 0.5, 1e-6, 12866
 WORKLOAD = ("roofline run: nz=2^20, nv=256, z in [-25600,25600), dt=0.4 dz, mu=10, omega=0, "
             "alpha=0.9, sigma=(0.6,0.5), random-phase seed 1e-6")
 
-# Algorithmic HBM bytes per real component per launch of each RK4 stage
-# (state y in double; stage increments in double (fp64) or float (mixed)):
-#   stage 1: read y, write d1; stage 2: read y, d1, write d2; stage 3: read y, d2,
-#   write d3; stage 4: read y, d3, d1, d2, write y.
-STAGE_BYTES = {"fp64": (16, 24, 24, 40), "mixed": (12, 16, 16, 28)}
+# Algorithmic HBM bytes per real component per launch of each RK4 stage.
+# fp64 (all arrays double): stage 1 reads y, writes d1; stage 2 reads y, d1,
+#   writes d2; stage 3 reads y, d2, writes d3; stage 4 reads y, d3, d1, d2 and
+#   writes y.
+# mixed (state y double plus its float copy y32; increments float): stages 1-3
+#   read y32 instead of y; stage 4 reads y32, d3 (window), y, d1, d2 (center)
+#   and writes y and y32.
+STAGE_BYTES = {"fp64": (16, 24, 24, 40), "mixed": (8, 12, 12, 36)}
 # Algorithmic FP64 flops per cell (4 reals) per launch of the fp64 stages
 # (moments, Hamiltonian, commutator, stencil, RK axpy; FMA = 2 flops).
 FP64_FLOPS_PER_CELL = {"fdko": (98, 106, 106, 138), "weno7": (482, 490, 490, 522)}
@@ -394,7 +398,8 @@ def run_ours(args, world, rank, local):
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if prec == "mixed" else "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "scheme": "FD+KO" if scheme == "fdko" else "WENO7",
+            "config": {"workload": WORKLOAD if NZ == NZ_FULL else f"PROFILING SIZE nz={NZ}",
+                       "scheme": "FD+KO" if scheme == "fdko" else "WENO7",
                        "precision": prec, "nz": NZ, "nv": NV, "cells_per_step": cells,
                        "l2": "inputs larger than L2 (state 17.2 GB >> 129 MB)",
                        "parallelism": f"replicas x{world}"},
@@ -420,7 +425,11 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=65536)
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--nz", type=int, default=NZ_FULL,
+                    help="z cells (smaller values only for profiling captures)")
     args = ap.parse_args()
+    global NZ, L
+    NZ, L = args.nz, args.nz * DZ
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     world, rank, local = dist_setup(args)

@@ -37,7 +37,7 @@ struct StageCfg {
 };
 
 struct Layout {
-  size_t y0, y1, d1, d2, d3, my, zavg, partial, result, err, total;
+  size_t y0, y1, y32a, y32b, d1, d2, d3, my, zavg, partial, result, err, total;
 };
 
 bool valid_sizes(int64_t nz, int32_t nv, int scheme, int precision) {
@@ -54,6 +54,9 @@ Layout make_layout(int64_t nz, int32_t nv, int precision) {
   size_t off = 0;
   L.y0 = off; off = align_up(off + n * sizeof(double));
   L.y1 = off; off = align_up(off + n * sizeof(double));
+  const size_t n32 = precision == COSENU_MIXED ? n : 0;  // float copies of y (mixed)
+  L.y32a = off; off = align_up(off + n32 * sizeof(float));
+  L.y32b = off; off = align_up(off + n32 * sizeof(float));
   L.d1 = off; off = align_up(off + n * dsz);
   L.d2 = off; off = align_up(off + n * dsz);
   L.d3 = off; off = align_up(off + n * dsz);
@@ -80,6 +83,7 @@ struct cosenu_s {
   unsigned char* ws = nullptr;
   Layout lay{};
   double* y[2] = {nullptr, nullptr};
+  float* y32[2] = {nullptr, nullptr};  // mixed: float copies of y[0], y[1]
   int ycur = 0;
   void* d[3] = {nullptr, nullptr, nullptr};
   double* my = nullptr;
@@ -204,6 +208,8 @@ StageArgs stage_args(cosenu_t h, int stage, int ycur) {
   a.weno_eps = h->p.weno_eps;
   a.y_in = h->y[ycur];
   a.y_out = h->y[ycur ^ 1];
+  a.y32_in = h->y32[ycur];
+  a.y32_out = h->y32[ycur ^ 1];
   a.my = h->my;
   a.err = h->err;
   switch (stage) {
@@ -328,6 +334,10 @@ cosenu_t create_common(int64_t nz, int32_t nv, double L, int scheme, int precisi
   h->own_stream = true;
   h->y[0] = reinterpret_cast<double*>(h->ws + h->lay.y0);
   h->y[1] = reinterpret_cast<double*>(h->ws + h->lay.y1);
+  if (precision == COSENU_MIXED) {
+    h->y32[0] = reinterpret_cast<float*>(h->ws + h->lay.y32a);
+    h->y32[1] = reinterpret_cast<float*>(h->ws + h->lay.y32b);
+  }
   h->d[0] = h->ws + h->lay.d1;
   h->d[1] = h->ws + h->lay.d2;
   h->d[2] = h->ws + h->lay.d3;
@@ -340,11 +350,16 @@ cosenu_t create_common(int64_t nz, int32_t nv, double L, int scheme, int precisi
   return h;
 }
 
-// Recompute the running FP64 moments of y after the state was replaced.
+// After the state was replaced: the mixed path's float copy of y and its
+// running FP64 moments.
 cudaError_t refresh_moments(cosenu_t h) {
+  if (h->precision != COSENU_MIXED) return cudaSuccess;
+  const int64_t n = 8 * h->nz * (int64_t)h->nv;
+  y32_from_y_kernel<<<(int)std::min<int64_t>((n + 255) / 256, 8192), 256, 0, h->stream>>>(
+      h->y[h->ycur], h->y32[h->ycur], n);
   ymoments_kernel<<<(int)std::min<int64_t>((h->nz + 7) / 8, 65535), 256, 0, h->stream>>>(
       h->y[h->ycur], h->nz, h->nv, h->my, 8);
-  g_launches.fetch_add(1, std::memory_order_relaxed);
+  g_launches.fetch_add(2, std::memory_order_relaxed);
   return cudaGetLastError();
 }
 

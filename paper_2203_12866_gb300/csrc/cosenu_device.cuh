@@ -45,8 +45,11 @@ struct StageArgs {
   double lambda;          // matter potential (nu: +, nubar: -)
   double ko_eps;
   double weno_eps;
-  const double* y_in;     // state at the start of the step (read with halo)
+  const double* y_in;     // state at the start of the step (fp64: read with halo;
+                          // mixed: center rows of stage 4 only)
   double* y_out;          // stage 4: state at the end of the step
+  const float* y32_in;    // mixed: float copy of y_in (read with halo)
+  float* y32_out;         // mixed, stage 4: float copy of y_out
   const void* d_in;       // stage s > 1: delta_{s-1} (read with halo)
   void* d_out;            // stages 1-3: delta_s
   const void* d1;         // stage 4: delta_1 (center rows only)
@@ -169,6 +172,52 @@ __device__ __forceinline__ T warp_sum6_transposed(const T (&m)[6]) {
   d += __shfl_xor_sync(0xffffffffu, d, 2);
   d += __shfl_xor_sync(0xffffffffu, d, 1);
   return d;
+}
+
+// ------------------------------------------------------------------ conversions
+// Conversions between double and float by integer arithmetic.  On GB300 the
+// hardware conversion runs on the FP64 pipe, which is 1/64 of the FP32 rate;
+// these keep the mixed path's state reads and updates off it.
+
+// double -> float, round to nearest even.  Magnitudes below the float normal
+// range (2^-126) become signed zero; above the float range, infinity; NaN
+// stays NaN.
+__device__ __forceinline__ float d2f_rn_int(double x) {
+  const uint32_t hi = (uint32_t)__double2hiint(x);
+  const uint32_t lo = (uint32_t)__double2loint(x);
+  const uint32_t sign = hi & 0x80000000u;
+  const uint32_t mag = hi & 0x7fffffffu;
+  // exponent rebased from the double bias (1023) to the float bias (127)
+  const int32_t t = (int32_t)mag - (int32_t)(896u << 20);
+  uint32_t r = ((uint32_t)t << 3) | (lo >> 29);
+  const uint32_t rem = lo & 0x1fffffffu;  // the 29 dropped mantissa bits
+  r += (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) ? 1u : 0u;
+  if (t < (int32_t)(1u << 20)) r = 0u;  // below the float normal range
+  if (t >= (int32_t)(255u << 20)) {     // overflow, infinity or NaN
+    const bool nan = mag > 0x7ff00000u || (mag == 0x7ff00000u && lo != 0u);
+    r = 0x7f800000u | (nan ? 0x00400000u : 0u);
+  }
+  return __uint_as_float(sign | r);
+}
+
+// float -> double, exact for normal floats; float subnormals become signed
+// zero; infinity and NaN are kept.
+__device__ __forceinline__ double f2d_int(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t sign = b & 0x80000000u;
+  const uint32_t mag = b & 0x7fffffffu;
+  uint32_t hi, lo;
+  if (mag < 0x00800000u) {
+    hi = sign;
+    lo = 0u;
+  } else if (mag >= 0x7f800000u) {
+    hi = sign | 0x7ff00000u | ((mag & 0x007fffffu) ? 0x00080000u : 0u);
+    lo = 0u;
+  } else {
+    hi = sign | ((mag >> 3) + (896u << 20));
+    lo = mag << 29;
+  }
+  return __hiloint2double((int)hi, (int)lo);
 }
 
 __device__ __forceinline__ bool is_finite_bits(double x) {

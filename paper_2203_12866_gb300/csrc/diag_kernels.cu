@@ -4,6 +4,8 @@
 // in a fixed order, so repeated calls on the same state give the same bits.
 #include "diag_kernels.cuh"
 
+#include "cosenu_device.cuh"
+
 namespace cosenu {
 
 // D_n = sum_j dv v_j^n (S_j - Sbar_j^*) of every z row, n = 0, 1 (Eq. (ham)).
@@ -43,6 +45,15 @@ __global__ void ymoments_kernel(const double* __restrict__ y, int64_t nz, int nv
     }
     if (lane >= 6 && lane < stride) out[z * stride + lane] = 0.0;
   }
+}
+
+// Float copy of the state for the mixed path's stencil window:
+// y32 = round-to-nearest float of y (same conversion as the stage kernels).
+__global__ void y32_from_y_kernel(const double* __restrict__ y, float* __restrict__ y32,
+                                  int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
+       e += (int64_t)gridDim.x * blockDim.x)
+    y32[e] = d2f_rn_int(y[e]);
 }
 
 // Column sums over z: out[q][v] = (1/nz) sum_z y[q][z][v].  Block = (q, 32 v);

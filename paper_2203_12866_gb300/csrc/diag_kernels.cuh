@@ -11,6 +11,8 @@ constexpr int kDiagMaxBlocks = 1024;
 
 __global__ void ymoments_kernel(const double* __restrict__ y, int64_t nz, int nv,
                                 double* __restrict__ out, int stride);
+__global__ void y32_from_y_kernel(const double* __restrict__ y, float* __restrict__ y32,
+                                  int64_t n);
 __global__ void zavg_kernel(const double* __restrict__ y, int64_t nz, int nv,
                             double* __restrict__ out);
 __global__ void conserved_partial_kernel(const double* __restrict__ y, int64_t nz, int nv,

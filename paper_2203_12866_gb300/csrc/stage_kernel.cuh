@@ -41,11 +41,13 @@ template <>
 struct Prec<kFP64> {
   using Real = double;   // stencil / commutator arithmetic
   using Delta = double;  // storage of stage increments
+  using WinY = double;   // state values entering the stencil window
 };
 template <>
 struct Prec<kMIXED> {
   using Real = float;
   using Delta = float;
+  using WinY = float;    // the float copy of y kept next to the FP64 state
 };
 
 template <int SCHEME>
@@ -74,12 +76,14 @@ struct SlotLayout {
 template <int PREC>
 __host__ __device__ inline SlotLayout slot_layout(int nv, int stage) {
   using Delta = typename Prec<PREC>::Delta;
+  using WinY = typename Prec<PREC>::WinY;
   SlotLayout L;
+  const int row_w = 8 * nv * (int)sizeof(WinY);
   const int row_y = 8 * nv * (int)sizeof(double);
   const int row_d = 8 * nv * (int)sizeof(Delta);
   int off = 0;
   L.y_off = off;
-  off += row_y;
+  off += row_w;
   L.din_off = off;
   if (stage > 1) off += row_d;
   L.yc_off = off;
@@ -259,7 +263,10 @@ __global__ void __launch_bounds__(kMaxThreads) rk4_stage_kernel(const StageArgs 
   // =================================================================== producer
   if (warp == ncw) {
     if (lane != 0) return;
-    const uint32_t ry = nv * sizeof(double), rd = nv * sizeof(Delta);
+    using WinY = typename Prec<PREC>::WinY;
+    const uint32_t rw = nv * sizeof(WinY), ry = nv * sizeof(double), rd = nv * sizeof(Delta);
+    const WinY* ywin = (PREC == kMIXED) ? reinterpret_cast<const WinY*>(a.y32_in)
+                                        : reinterpret_cast<const WinY*>(a.y_in);
     const Delta* din = static_cast<const Delta*>(a.d_in);
     const Delta* d1 = static_cast<const Delta*>(a.d1);
     const Delta* d2 = static_cast<const Delta*>(a.d2);
@@ -277,15 +284,15 @@ __global__ void __launch_bounds__(kMaxThreads) rk4_stage_kernel(const StageArgs 
       const int64_t c = i - LAG;
       const bool has_center = (STAGE == 4) && c >= z_begin && c < z_end;
       const bool has_my = (PREC == kMIXED) && i >= z_begin && i < z_end;
-      uint32_t tx = 8 * ry + (STAGE > 1 ? 8 * rd : 0);
+      uint32_t tx = 8 * rw + (STAGE > 1 ? 8 * rd : 0);
       if (has_center) tx += 8 * ry + 16 * rd;
       if (has_my) tx += 64;
       mbar_arrive_expect_tx(bar, tx);
       const int64_t plane = nz * nv;
-      const double* ysrc = a.y_in + r * nv;
+      const WinY* ysrc = ywin + r * nv;
 #pragma unroll 1
       for (int q = 0; q < 8; ++q) {
-        bulk_g2s(base + L.y_off + q * ry, ysrc + q * plane, ry, bar);
+        bulk_g2s(base + L.y_off + q * rw, ysrc + q * plane, rw, bar);
         if (STAGE > 1) bulk_g2s(base + L.din_off + q * rd, din + r * nv + q * plane, rd, bar);
       }
       if (has_center) {
@@ -395,18 +402,16 @@ __global__ void __launch_bounds__(kMaxThreads) rk4_stage_kernel(const StageArgs 
     double yc[4];
     Real e1[4], e2[4];
     {
-      const double* ys = reinterpret_cast<const double*>(sb + L.y_off);
+      using WinY = typename Prec<PREC>::WinY;
+      const WinY* ys = reinterpret_cast<const WinY*>(sb + L.y_off);
       const Delta* ds = reinterpret_cast<const Delta*>(sb + L.din_off);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int e = ecol + q * nv;
-        const double yv = active ? ys[e] : 0.0;
+        const WinY yv = active ? ys[e] : WinY(0);
         const Delta dd = (STAGE > 1 && active) ? ds[e] : Delta(0);
         draw[q] = Real(dd);
-        if (PREC == kFP64)
-          unew[q] = Real(yv + double(dd));
-        else
-          unew[q] = Real(float(yv) + float(dd));
+        unew[q] = Real(yv + dd);  // fp64: y + delta; mixed: float(y) + delta
       }
       if (STAGE == 4 && center_in_range) {
         const double* ycs = reinterpret_cast<const double*>(sb + L.yc_off);
@@ -525,9 +530,13 @@ __global__ void __launch_bounds__(kMaxThreads) rk4_stage_kernel(const StageArgs 
             e3 = dring[0][q];
           incr[q] = (e1[q] + Real(2) * e2[q] + e3) * Real(1.0 / 3.0) +
                     (dt * Real(1.0 / 6.0)) * kk[q];
-          const double ynew = yc[q] + double(incr[q]);
+          const double ynew =
+              yc[q] + (PREC == kFP64 ? double(incr[q]) : f2d_int(float(incr[q])));
           bad |= !is_finite_bits(ynew);
-          if (active) a.y_out[gout + (int64_t)q * plane] = ynew;
+          if (active) {
+            a.y_out[gout + (int64_t)q * plane] = ynew;
+            if (PREC == kMIXED) a.y32_out[gout + (int64_t)q * plane] = d2f_rn_int(ynew);
+          }
         }
         nonfinite |= bad;
         if (PREC == kMIXED) {
