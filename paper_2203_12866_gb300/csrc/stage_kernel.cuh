@@ -31,6 +31,8 @@
 //    increment in stage 4); D_n(delta) is summed in float.
 #pragma once
 
+#include <type_traits>
+
 #include "cosenu_device.cuh"
 
 namespace cosenu {
@@ -54,23 +56,25 @@ template <int SCHEME>
 struct Scheme;
 template <>
 struct Scheme<kFDKO> {
-  static constexpr int kLag = 2;  // center = leading row - 2
-  static constexpr int kWin = 5;  // rows c-2 .. c+2
-  static constexpr int kLo = 2;   // halo rows before the first center
-  static constexpr int kHi = 2;   // halo rows after the last center
+  static constexpr int kLag = 2;     // center = leading row - 2
+  static constexpr int kWin = 5;     // rows c-2 .. c+2
+  static constexpr int kLo = 2;      // halo rows before the first center
+  static constexpr int kHi = 2;      // halo rows after the last center
+  static constexpr bool kRing = true;  // unroll the march by kWin (window as a ring)
 };
 template <>
 struct Scheme<kWENO7> {
-  static constexpr int kLag = 4;  // center = leading row - 4
-  static constexpr int kWin = 8;  // rows c-3 .. c+4 (face c+1/2 of either upwind side)
-  static constexpr int kLo = 4;   // face z_begin - 1/2 needs rows from z_begin - 4
+  static constexpr int kLag = 4;     // center = leading row - 4
+  static constexpr int kWin = 8;     // rows c-3 .. c+4 (face c+1/2 of either upwind side)
+  static constexpr int kLo = 4;      // face z_begin - 1/2 needs rows from z_begin - 4
   static constexpr int kHi = 4;
+  static constexpr bool kRing = false;  // body too large to unroll: shift the window
 };
 
 // Byte layout of one ring slot.  Window arrays belong to the leading row i,
 // center arrays (stage 4 only) to the row i - lag.
 struct SlotLayout {
-  int y_off, din_off, yc_off, d1c_off, d2c_off, my_off, bytes;
+  int y_off, din_off, yc_off, d1c_off, d2c_off, d3c_off, my_off, bytes;
 };
 
 template <int PREC>
@@ -92,6 +96,8 @@ __host__ __device__ inline SlotLayout slot_layout(int nv, int stage) {
   if (stage == 4) off += row_d;
   L.d2c_off = off;
   if (stage == 4) off += row_d;
+  L.d3c_off = off;  // mixed: delta_3 of the center row (the window holds y + delta_3)
+  if (stage == 4 && PREC == kMIXED) off += row_d;
   L.my_off = off;
   if (PREC == kMIXED) off += 8 * (int)sizeof(double);
   L.bytes = (off + 127) & ~127;
@@ -122,9 +128,21 @@ __host__ __device__ inline int stage_smem_header_bytes() {
   return SmemHeader<PREC>::kBytes;
 }
 
+// Calls f(std::integral_constant<int, K>) for K = B .. E-1 (compile-time unrolled).
+template <int B, int E, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (B < E) {
+    f(std::integral_constant<int, B>{});
+    static_for<B + 1, E>(f);
+  }
+}
+
+// Periodic row index without a division: rows reach at most a few cells past
+// either end of [0, nz) (more turns only on grids shorter than the stencil).
 __device__ __forceinline__ int64_t wrap_row(int64_t r, int64_t nz) {
-  int64_t m = r % nz;
-  return m < 0 ? m + nz : m;
+  while (r < 0) r += nz;
+  while (r >= nz) r -= nz;
+  return r;
 }
 
 // ---------------------------------------------------------------- WENO7 face
@@ -271,10 +289,10 @@ __global__ void __launch_bounds__(kMaxThreads) rk4_stage_kernel(const StageArgs 
     const Delta* d1 = static_cast<const Delta*>(a.d1);
     const Delta* d2 = static_cast<const Delta*>(a.d2);
     int64_t issued = 0;
+    int slot = 0;
+    uint32_t fill = 0;  // how many times this slot has been filled before
     for (int64_t j = 0; j < nrows; ++j) {
-      const int slot = (int)(j % D);
-      const int64_t n = j / D;
-      if (n > 0 && !mbar_wait_or_abort(empty_bar(slot), (uint32_t)((n - 1) & 1), abort_flag, a.err))
+      if (fill > 0 && !mbar_wait_or_abort(empty_bar(slot), (fill - 1) & 1u, abort_flag, a.err))
         break;
       fence_proxy_async();
       const uint32_t bar = full_bar(slot);
@@ -285,7 +303,7 @@ __global__ void __launch_bounds__(kMaxThreads) rk4_stage_kernel(const StageArgs 
       const bool has_center = (STAGE == 4) && c >= z_begin && c < z_end;
       const bool has_my = (PREC == kMIXED) && i >= z_begin && i < z_end;
       uint32_t tx = 8 * rw + (STAGE > 1 ? 8 * rd : 0);
-      if (has_center) tx += 8 * ry + 16 * rd;
+      if (has_center) tx += 8 * ry + (PREC == kMIXED ? 24 : 16) * rd;
       if (has_my) tx += 64;
       mbar_arrive_expect_tx(bar, tx);
       const int64_t plane = nz * nv;
@@ -302,10 +320,15 @@ __global__ void __launch_bounds__(kMaxThreads) rk4_stage_kernel(const StageArgs 
           bulk_g2s(base + L.yc_off + q * ry, a.y_in + o, ry, bar);
           bulk_g2s(base + L.d1c_off + q * rd, d1 + o, rd, bar);
           bulk_g2s(base + L.d2c_off + q * rd, d2 + o, rd, bar);
+          if (PREC == kMIXED) bulk_g2s(base + L.d3c_off + q * rd, din + o, rd, bar);
         }
       }
       if (has_my) bulk_g2s(base + L.my_off, a.my + i * 8, 64, bar);
       issued = j + 1;
+      if (++slot == D) {
+        slot = 0;
+        ++fill;
+      }
     }
     // Leave only after the last fill of every slot has landed (each wait bounded).
     for (int64_t j = (issued > D ? issued - D : 0); j < issued; ++j)
@@ -373,34 +396,55 @@ __global__ void __launch_bounds__(kMaxThreads) rk4_stage_kernel(const StageArgs 
   const int64_t plane = nz * nv;
   const int ecol = s * 4 * nv + vj;  // element of component 0 in a slot row
 
+  // Sliding window of this column: u[k] holds one row; the loop is unrolled
+  // by WIN so that the ring position of every row is a compile-time index.
   Real u[WIN][4];
 #pragma unroll
   for (int k = 0; k < WIN; ++k)
 #pragma unroll
     for (int q = 0; q < 4; ++q) u[k][q] = Real(0);
-  Real dring[LAG + 1][4];  // mixed stage 4: raw delta_3 of the last lag+1 rows
-#pragma unroll
-  for (int k = 0; k <= LAG; ++k)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) dring[k][q] = Real(0);
   Real fprev[4] = {Real(0), Real(0), Real(0), Real(0)};  // WENO flux at c - 1/2
   bool nonfinite = false;
+  bool stop = false;
+  int slot = 0;
+  uint32_t par = 0;  // phase parity of the current slot
+  Delta* dout = static_cast<Delta*>(a.d_out) + (int64_t)(s * 4) * plane + vj;
+  double* yout = a.y_out + (int64_t)(s * 4) * plane + vj;
+  float* y32out = a.y32_out + (int64_t)(s * 4) * plane + vj;
 
-#pragma unroll 1
-  for (int64_t j = 0; j < nrows; ++j) {
+  constexpr bool RING = Scheme<SCHEME>::kRing;
+  auto row = [&](auto kc, int64_t j) {
+    // Ring: the entering row goes to u[K] and window row m (0 = oldest) sits at
+    // u[(K + 1 + m) % WIN].  Shift register: rows move down one place per
+    // iteration and the entering row goes to u[WIN - 1].
+    constexpr int K = RING ? decltype(kc)::value : WIN - 1;
+    constexpr int O = RING ? K + 1 : 0;
+    constexpr int W0 = (O + 0) % WIN, W1 = (O + 1) % WIN, W2 = (O + 2) % WIN,
+                  W3 = (O + 3) % WIN, W4 = (O + 4) % WIN, W5 = (O + 5) % WIN,
+                  W6 = (O + 6) % WIN, W7 = (O + 7) % WIN;
+    if (!RING) {
+#pragma unroll
+      for (int k = 0; k < WIN - 1; ++k)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) u[k][q] = u[k + 1][q];
+    }
     const int64_t i = i_first + j;
-    const int slot = (int)(j % D);
-    const unsigned char* sb = ring + (size_t)slot * a.slot_bytes;
     const int64_t c = i - LAG;
-    const bool lead_in_range = i >= z_begin && i < z_end;
-    const bool center_in_range = c >= z_begin && c < z_end;
+    const int rl = (int)(i - z_begin);  // relative leading row
+    const int rc = rl - LAG;            // relative center row
+    const bool lead_in_range = rl >= 0 && i < z_end;
+    const bool center_in_range = rc >= 0 && c < z_end;
+    const unsigned char* sb = ring + (size_t)slot * a.slot_bytes;
 
-    if (!warp_wait(full_bar(slot), (uint32_t)((j / D) & 1))) break;
+    if (!warp_wait(full_bar(slot), par)) {
+      stop = true;
+      return;
+    }
 
     // ---- read the slot: leading row i (window arrays), center row c (stage 4)
-    Real unew[4], draw[4];
-    double yc[4];
-    Real e1[4], e2[4];
+    Real draw[4] = {0, 0, 0, 0};
+    double yc[4] = {0, 0, 0, 0};
+    Real e1[4] = {0, 0, 0, 0}, e2[4] = {0, 0, 0, 0}, e3[4] = {0, 0, 0, 0};
     {
       using WinY = typename Prec<PREC>::WinY;
       const WinY* ys = reinterpret_cast<const WinY*>(sb + L.y_off);
@@ -411,50 +455,43 @@ __global__ void __launch_bounds__(kMaxThreads) rk4_stage_kernel(const StageArgs 
         const WinY yv = active ? ys[e] : WinY(0);
         const Delta dd = (STAGE > 1 && active) ? ds[e] : Delta(0);
         draw[q] = Real(dd);
-        unew[q] = Real(yv + dd);  // fp64: y + delta; mixed: float(y) + delta
+        u[K][q] = Real(yv + dd);  // fp64: y + delta; mixed: float(y) + delta
       }
       if (STAGE == 4 && center_in_range) {
         const double* ycs = reinterpret_cast<const double*>(sb + L.yc_off);
         const Delta* d1s = reinterpret_cast<const Delta*>(sb + L.d1c_off);
         const Delta* d2s = reinterpret_cast<const Delta*>(sb + L.d2c_off);
+        const Delta* d3s = reinterpret_cast<const Delta*>(sb + L.d3c_off);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int e = ecol + q * nv;
           yc[q] = active ? ycs[e] : 0.0;
           e1[q] = active ? Real(d1s[e]) : Real(0);
           e2[q] = active ? Real(d2s[e]) : Real(0);
+          if (PREC == kMIXED) e3[q] = active ? Real(d3s[e]) : Real(0);
         }
       }
       if (PREC == kMIXED && warp == 0 && lane < 6 && lead_in_range)
-        myring[(int)((i - z_begin) % MS) * 8 + lane] =
-            reinterpret_cast<const double*>(sb + L.my_off)[lane];
+        myring[(rl & (MS - 1)) * 8 + lane] = reinterpret_cast<const double*>(sb + L.my_off)[lane];
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(empty_bar(slot));
-
-#pragma unroll
-    for (int k = 0; k < WIN - 1; ++k)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) u[k][q] = u[k + 1][q];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) u[WIN - 1][q] = unew[q];
-    if (PREC == kMIXED && STAGE == 4) {
-#pragma unroll
-      for (int k = 0; k < LAG; ++k)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) dring[k][q] = dring[k + 1][q];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) dring[LAG][q] = draw[q];
+    if (++slot == D) {
+      slot = 0;
+      par ^= 1u;
     }
 
     // ---- partial velocity moments of row i (finished by the reducer)
     if (lead_in_range) {
-      const int m = (int)((i - z_begin) % MS);
+      const int m = rl & (MS - 1);
       if (PREC == kFP64 || STAGE > 1) {
-        const Real* src = (PREC == kFP64) ? unew : draw;
-        const Real t3 = src[0] - src[1];
-        const Real m6[6] = {w3 * t3, w3v * t3, w3 * src[2], w3v * src[2], wi * src[3],
-                            wiv * src[3]};
+        // fp64: moments of u itself; mixed: of the increment (y's are running sums)
+        const Real s0 = (PREC == kFP64) ? u[K][0] : draw[0];
+        const Real s1 = (PREC == kFP64) ? u[K][1] : draw[1];
+        const Real s2 = (PREC == kFP64) ? u[K][2] : draw[2];
+        const Real s3 = (PREC == kFP64) ? u[K][3] : draw[3];
+        const Real t3 = s0 - s1;
+        const Real m6[6] = {w3 * t3, w3v * t3, w3 * s2, w3v * s2, wi * s3, wiv * s3};
         const Real tot = warp_sum6_transposed(m6);
         const int k = (lane >> 2) & 7;
         if ((lane & 3) == 0 && k < 6) part[(m * kMaxWarps + warp) * 8 + k] = tot;
@@ -465,29 +502,33 @@ __global__ void __launch_bounds__(kMaxThreads) rk4_stage_kernel(const StageArgs 
 
     // ---- center row c = i - lag
     Real fcur[4] = {Real(0), Real(0), Real(0), Real(0)};
-    if (SCHEME == kWENO7 && c >= z_begin - 1 && c < z_end) {
+    if (SCHEME == kWENO7 && rc >= -1 && c < z_end) {
       // flux F_{c+1/2} = v * WENO(u), upwind by the sign of v
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         Real r;
         if (upwind_left)
-          r = weno7_face(u[0][q], u[1][q], u[2][q], u[3][q], u[4][q], u[5][q], u[6][q], eps_v);
+          r = weno7_face(u[W0][q], u[W1][q], u[W2][q], u[W3][q], u[W4][q], u[W5][q], u[W6][q],
+                         eps_v);
         else
-          r = weno7_face(u[7][q], u[6][q], u[5][q], u[4][q], u[3][q], u[2][q], u[1][q], eps_v);
+          r = weno7_face(u[W7][q], u[W6][q], u[W5][q], u[W4][q], u[W3][q], u[W2][q], u[W1][q],
+                         eps_v);
         fcur[q] = v * r;
       }
     }
     if (center_in_range) {
-      const int64_t rc = c - z_begin;
-      const int m = (int)(rc % MS);
-      if (!warp_wait(mom_bar(m), (uint32_t)((rc / MS) & 1))) break;
+      const int m = rc & (MS - 1);
+      if (!warp_wait(mom_bar(m), (uint32_t)((rc / MS) & 1))) {
+        stop = true;
+        return;
+      }
       const Acc* mf = momf + m * 8;
       const Real D30 = Real(mf[0]), D31 = Real(mf[1]), Dr0 = Real(mf[2]), Dr1 = Real(mf[3]),
                  Di0 = Real(mf[4]), Di1 = Real(mf[5]);
       const Real dH = hd0 + mus * (D30 - v * D31);
       const Real hr = hr0 + mus * (Dr0 - v * Dr1);
       const Real hi = mu * (Di0 - v * Di1);
-      constexpr int CC = (SCHEME == kFDKO) ? 2 : 3;  // center index in the window
+      constexpr int CC = (SCHEME == kFDKO) ? W2 : W3;  // the center row in the window
       const Real ua = u[CC][0], ub = u[CC][1], ucr = u[CC][2], uci = u[CC][3];
       const Real amb = ua - ub;
       Real kk[4];
@@ -501,7 +542,8 @@ __global__ void __launch_bounds__(kMaxThreads) rk4_stage_kernel(const StageArgs 
       for (int q = 0; q < 4; ++q) {
         Real adv;
         if (SCHEME == kFDKO) {
-          const Real um2 = u[0][q], um1 = u[1][q], u0 = u[2][q], up1 = u[3][q], up2 = u[4][q];
+          const Real um2 = u[W0][q], um1 = u[W1][q], u0 = u[W2][q], up1 = u[W3][q],
+                     up2 = u[W4][q];
           const Real fd = Real(8) * (up1 - um1) - (up2 - um2);
           const Real ko = (um2 + up2) - Real(4) * (um1 + up1) + Real(6) * u0;
           adv = c_fd * fd + c_ko * ko;
@@ -510,32 +552,31 @@ __global__ void __launch_bounds__(kMaxThreads) rk4_stage_kernel(const StageArgs 
         }
         kk[q] += adv;
       }
-      const int64_t gout = (int64_t)(s * 4) * plane + c * nv + vj;  // component 0, row c
+      const int64_t rowoff = c * nv;
       if (STAGE < 4) {
-        Delta* dout = static_cast<Delta*>(a.d_out);
         const Real f = (STAGE == 3) ? dt : Real(0.5) * dt;
         if (active) {
 #pragma unroll
-          for (int q = 0; q < 4; ++q) dout[gout + (int64_t)q * plane] = Delta(f * kk[q]);
+          for (int q = 0; q < 4; ++q) dout[rowoff + (int64_t)q * plane] = Delta(f * kk[q]);
         }
       } else {
         Real incr[4];
         bool bad = false;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          Real e3;
+          Real d3;
           if (PREC == kFP64)
-            e3 = Real(double(u[CC][q]) - yc[q]);  // u = y + delta_3 at the center
+            d3 = Real(double(u[CC][q]) - yc[q]);  // u = y + delta_3 at the center
           else
-            e3 = dring[0][q];
-          incr[q] = (e1[q] + Real(2) * e2[q] + e3) * Real(1.0 / 3.0) +
+            d3 = e3[q];
+          incr[q] = (e1[q] + Real(2) * e2[q] + d3) * Real(1.0 / 3.0) +
                     (dt * Real(1.0 / 6.0)) * kk[q];
           const double ynew =
               yc[q] + (PREC == kFP64 ? double(incr[q]) : f2d_int(float(incr[q])));
           bad |= !is_finite_bits(ynew);
           if (active) {
-            a.y_out[gout + (int64_t)q * plane] = ynew;
-            if (PREC == kMIXED) a.y32_out[gout + (int64_t)q * plane] = d2f_rn_int(ynew);
+            yout[rowoff + (int64_t)q * plane] = ynew;
+            if (PREC == kMIXED) y32out[rowoff + (int64_t)q * plane] = d2f_rn_int(ynew);
           }
         }
         nonfinite |= bad;
@@ -556,6 +597,19 @@ __global__ void __launch_bounds__(kMaxThreads) rk4_stage_kernel(const StageArgs 
 #pragma unroll
       for (int q = 0; q < 4; ++q) fprev[q] = fcur[q];
     }
+  };
+
+  if constexpr (RING) {
+#pragma unroll 1
+    for (int64_t jb = 0; jb < nrows && !stop; jb += WIN) {
+      static_for<0, WIN>([&](auto kc) {
+        const int64_t j = jb + decltype(kc)::value;
+        if (j < nrows && !stop) row(kc, j);
+      });
+    }
+  } else {
+#pragma unroll 1
+    for (int64_t j = 0; j < nrows && !stop; ++j) row(std::integral_constant<int, 0>{}, j);
   }
 
   if (STAGE == 4) {
