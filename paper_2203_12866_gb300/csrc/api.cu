@@ -141,6 +141,14 @@ int max_blocks(cosenu_t h, int stage, int block, size_t smem) {
   return stage_max_blocks_per_sm<kWENO7, kMIXED>(stage, block, smem);
 }
 
+int cols_per_thread(cosenu_t h) {
+  if (h->scheme == COSENU_FDKO)
+    return h->precision == COSENU_FP64 ? cosenu::stage_cols<kFDKO, kFP64>()
+                                       : cosenu::stage_cols<kFDKO, kMIXED>();
+  return h->precision == COSENU_FP64 ? cosenu::stage_cols<kWENO7, kFP64>()
+                                     : cosenu::stage_cols<kWENO7, kMIXED>();
+}
+
 int slot_bytes(cosenu_t h, int stage) {
   return h->precision == COSENU_FP64 ? slot_layout<kFP64>(h->nv, stage).bytes
                                      : slot_layout<kMIXED>(h->nv, stage).bytes;
@@ -158,7 +166,9 @@ int configure(cosenu_t h) {
                                                  : stage_smem_header_bytes<kMIXED>();
   for (int s = 1; s <= 4; ++s) {
     StageCfg c;
-    c.block = ((2 * h->nv + 31) / 32) * 32 + 64;  // consumers + producer + reducer warps
+    // consumer warps (cols adjacent columns per thread) + producer + reducer warps
+    const int cols = cols_per_thread(h);
+    c.block = ((2 * h->nv + 32 * cols - 1) / (32 * cols)) * 32 + 64;
     c.slot_bytes = slot_bytes(h, s);
     int best_occ = 0, best_d = 0;
     for (int D = 2; D <= kMaxRing; ++D) {

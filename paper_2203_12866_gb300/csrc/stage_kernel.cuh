@@ -71,6 +71,42 @@ struct Scheme<kWENO7> {
   static constexpr bool kRing = false;  // body too large to unroll: shift the window
 };
 
+// Adjacent v-columns per consumer thread.  Two (FD4 + KO): vector shared-memory
+// and global accesses, and the per-row waits, arrivals and moment shuffles are
+// shared by both columns.  One (WENO7): the reconstruction is arithmetic-heavy
+// and needs the latency hiding of twice as many warps (and its FP64 window
+// would not fit in the registers twice).
+template <int SCHEME, int PREC>
+__host__ __device__ constexpr int stage_cols() {
+  return SCHEME == kWENO7 ? 1 : 2;
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void vload(const T* p, T (&out)[N]) {
+  if constexpr (N == 1) {
+    out[0] = p[0];
+  } else if constexpr (sizeof(T) == 4) {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    out[0] = t.x;
+    out[1] = t.y;
+  } else {
+    const double2 t = *reinterpret_cast<const double2*>(p);
+    out[0] = t.x;
+    out[1] = t.y;
+  }
+}
+
+template <typename T, int N>
+__device__ __forceinline__ void vstore(T* p, const T (&in)[N]) {
+  if constexpr (N == 1) {
+    p[0] = in[0];
+  } else if constexpr (sizeof(T) == 4) {
+    *reinterpret_cast<float2*>(p) = make_float2(in[0], in[1]);
+  } else {
+    *reinterpret_cast<double2*>(p) = make_double2(in[0], in[1]);
+  }
+}
+
 // Byte layout of one ring slot.  Window arrays belong to the leading row i,
 // center arrays (stage 4 only) to the row i - lag.
 struct SlotLayout {
@@ -214,8 +250,16 @@ __device__ __forceinline__ float weno7_face(float fm3, float fm2, float fm1, flo
 
 // ---------------------------------------------------------------- the kernel
 
+// Largest CTA of a stage kernel: consumer warps for 256 v-columns per species,
+// plus the producer and reducer warps.
+template <int SCHEME, int PREC>
+__host__ __device__ constexpr int stage_max_threads() {
+  return (kMaxWarps / stage_cols<SCHEME, PREC>() + 2) * 32;
+}
+
 template <int SCHEME, int PREC, int STAGE>
-__global__ void __launch_bounds__(kMaxThreads) rk4_stage_kernel(const StageArgs a) {
+__global__ void __launch_bounds__(stage_max_threads<SCHEME, PREC>())
+    rk4_stage_kernel(const StageArgs a) {
   using Real = typename Prec<PREC>::Real;
   using Delta = typename Prec<PREC>::Delta;
   using Acc = Real;
@@ -237,7 +281,8 @@ __global__ void __launch_bounds__(kMaxThreads) rk4_stage_kernel(const StageArgs 
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int warp = tid >> 5;
-  const int ncw = (a.ncols + 31) >> 5;  // consumer warps; then producer, reducer
+  constexpr int COLS = stage_cols<SCHEME, PREC>();
+  const int ncw = (a.ncols + 32 * COLS - 1) / (32 * COLS);  // consumer warps; then producer, reducer
   const int64_t nz = a.nz;
   const int nv = a.nv;
   const SlotLayout L = slot_layout<PREC>(nv, STAGE);
@@ -369,48 +414,61 @@ __global__ void __launch_bounds__(kMaxThreads) rk4_stage_kernel(const StageArgs 
   }
 
   // =================================================================== consumers
-  const bool active = tid < a.ncols;
-  const int s = active ? tid / nv : 0;  // species
-  const int vj = active ? tid % nv : 0;
+  // Thread t owns the COLS adjacent columns 2t.. of one species (nv is a
+  // multiple of 4, so the pair never straddles the species boundary).
+  const int col0 = tid * COLS;
+  const bool active = col0 < a.ncols;
+  const int s = active ? col0 / nv : 0;  // species
+  const int vj0 = active ? col0 % nv : 0;
   const double dv = 2.0 / nv;
-  const double vd = -1.0 + (vj + 0.5) * dv;
-  const Real v = Real(vd);
   const double sgn = (s == 0) ? 1.0 : -1.0;
-  // moment weights: D3 and Dr take + for nu and - for nubar, Di takes + for both
-  const Real w3 = active ? Real(sgn * dv) : Real(0);
-  const Real w3v = active ? Real(sgn * dv * vd) : Real(0);
-  const Real wi = active ? Real(dv) : Real(0);
-  const Real wiv = active ? Real(dv * vd) : Real(0);
+  Real v[COLS], w3[COLS], w3v[COLS], wi[COLS], wiv[COLS], c_fd[COLS], eps_v[COLS];
+  bool upwind_left[COLS];
+#pragma unroll
+  for (int cc = 0; cc < COLS; ++cc) {
+    const double vd = -1.0 + (vj0 + cc + 0.5) * dv;
+    v[cc] = Real(vd);
+    // moment weights: D3 and Dr take + for nu and - for nubar, Di takes + for both
+    w3[cc] = active ? Real(sgn * dv) : Real(0);
+    w3v[cc] = active ? Real(sgn * dv * vd) : Real(0);
+    wi[cc] = active ? Real(dv) : Real(0);
+    wiv[cc] = active ? Real(dv * vd) : Real(0);
+    c_fd[cc] = Real(-vd * a.inv_dz / 12.0);
+    eps_v[cc] = Real(a.weno_eps / (vd * vd));  // WENO_eps(v u) = v WENO_{eps/v^2}(u)
+    upwind_left[cc] = vd > 0.0;
+  }
   // H = (hvac_d + sgn lambda + sgn mu (D3_0 - v D3_1), hvac_r + sgn mu (Dr_0 - v Dr_1),
   //      mu (Di_0 - v Di_1)) for (H_ee - H_xx, Re H_ex, Im H_ex)
   const Real hd0 = Real(a.hvac_d + sgn * a.lambda);
   const Real hr0 = Real(a.hvac_r);
   const Real mus = Real(sgn * a.mu);
   const Real mu = Real(a.mu);
-  const Real c_fd = Real(-vd * a.inv_dz / 12.0);
   const Real c_ko = Real(-a.ko_eps * a.inv_dz / 16.0);
   const Real inv_dz = Real(a.inv_dz);
-  const Real eps_v = Real(a.weno_eps / (vd * vd));  // WENO_eps(v u) = v WENO_{eps/v^2}(u)
-  const bool upwind_left = vd > 0.0;
   const Real dt = Real(a.dt);
   const int64_t plane = nz * nv;
-  const int ecol = s * 4 * nv + vj;  // element of component 0 in a slot row
+  const int ecol = s * 4 * nv + vj0;  // element of component 0 in a slot row
 
-  // Sliding window of this column: u[k] holds one row; the loop is unrolled
-  // by WIN so that the ring position of every row is a compile-time index.
-  Real u[WIN][4];
+  // Sliding window of this thread's columns: u[k] holds one row.
+  Real u[WIN][4][COLS];
 #pragma unroll
   for (int k = 0; k < WIN; ++k)
 #pragma unroll
-    for (int q = 0; q < 4; ++q) u[k][q] = Real(0);
-  Real fprev[4] = {Real(0), Real(0), Real(0), Real(0)};  // WENO flux at c - 1/2
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int cc = 0; cc < COLS; ++cc) u[k][q][cc] = Real(0);
+  Real fprev[4][COLS];  // WENO flux at c - 1/2
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int cc = 0; cc < COLS; ++cc) fprev[q][cc] = Real(0);
   bool nonfinite = false;
   bool stop = false;
   int slot = 0;
   uint32_t par = 0;  // phase parity of the current slot
-  Delta* dout = static_cast<Delta*>(a.d_out) + (int64_t)(s * 4) * plane + vj;
-  double* yout = a.y_out + (int64_t)(s * 4) * plane + vj;
-  float* y32out = a.y32_out + (int64_t)(s * 4) * plane + vj;
+  Delta* dout = static_cast<Delta*>(a.d_out) + (int64_t)(s * 4) * plane + vj0;
+  double* yout = a.y_out + (int64_t)(s * 4) * plane + vj0;
+  float* y32out = a.y32_out + (int64_t)(s * 4) * plane + vj0;
 
   constexpr bool RING = Scheme<SCHEME>::kRing;
   auto row = [&](auto kc, int64_t j) {
@@ -426,7 +484,9 @@ __global__ void __launch_bounds__(kMaxThreads) rk4_stage_kernel(const StageArgs 
 #pragma unroll
       for (int k = 0; k < WIN - 1; ++k)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) u[k][q] = u[k + 1][q];
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int cc = 0; cc < COLS; ++cc) u[k][q][cc] = u[k + 1][q][cc];
     }
     const int64_t i = i_first + j;
     const int64_t c = i - LAG;
@@ -442,9 +502,17 @@ __global__ void __launch_bounds__(kMaxThreads) rk4_stage_kernel(const StageArgs 
     }
 
     // ---- read the slot: leading row i (window arrays), center row c (stage 4)
-    Real draw[4] = {0, 0, 0, 0};
-    double yc[4] = {0, 0, 0, 0};
-    Real e1[4] = {0, 0, 0, 0}, e2[4] = {0, 0, 0, 0}, e3[4] = {0, 0, 0, 0};
+    Real draw[4][COLS];
+    double yc[4][COLS];
+    Real e1[4][COLS], e2[4][COLS], e3[4][COLS];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int cc = 0; cc < COLS; ++cc) {
+        draw[q][cc] = Real(0);
+        yc[q][cc] = 0.0;
+        e1[q][cc] = e2[q][cc] = e3[q][cc] = Real(0);
+      }
     {
       using WinY = typename Prec<PREC>::WinY;
       const WinY* ys = reinterpret_cast<const WinY*>(sb + L.y_off);
@@ -452,12 +520,24 @@ __global__ void __launch_bounds__(kMaxThreads) rk4_stage_kernel(const StageArgs 
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const int e = ecol + q * nv;
-        const WinY yv = active ? ys[e] : WinY(0);
-        const Delta dd = (STAGE > 1 && active) ? ds[e] : Delta(0);
-        draw[q] = Real(dd);
-        u[K][q] = Real(yv + dd);  // fp64: y + delta; mixed: float(y) + delta
+        WinY yv[COLS];
+        Delta dd[COLS];
+#pragma unroll
+        for (int cc = 0; cc < COLS; ++cc) {
+          yv[cc] = WinY(0);
+          dd[cc] = Delta(0);
+        }
+        if (active) {
+          vload(ys + e, yv);
+          if (STAGE > 1) vload(ds + e, dd);
+        }
+#pragma unroll
+        for (int cc = 0; cc < COLS; ++cc) {
+          draw[q][cc] = Real(dd[cc]);
+          u[K][q][cc] = Real(yv[cc] + dd[cc]);  // fp64: y + delta; mixed: float(y) + delta
+        }
       }
-      if (STAGE == 4 && center_in_range) {
+      if (STAGE == 4 && center_in_range && active) {
         const double* ycs = reinterpret_cast<const double*>(sb + L.yc_off);
         const Delta* d1s = reinterpret_cast<const Delta*>(sb + L.d1c_off);
         const Delta* d2s = reinterpret_cast<const Delta*>(sb + L.d2c_off);
@@ -465,10 +545,17 @@ __global__ void __launch_bounds__(kMaxThreads) rk4_stage_kernel(const StageArgs 
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           const int e = ecol + q * nv;
-          yc[q] = active ? ycs[e] : 0.0;
-          e1[q] = active ? Real(d1s[e]) : Real(0);
-          e2[q] = active ? Real(d2s[e]) : Real(0);
-          if (PREC == kMIXED) e3[q] = active ? Real(d3s[e]) : Real(0);
+          Delta t1[COLS], t2[COLS], t3[COLS];
+          vload(ycs + e, yc[q]);
+          vload(d1s + e, t1);
+          vload(d2s + e, t2);
+          if (PREC == kMIXED) vload(d3s + e, t3);
+#pragma unroll
+          for (int cc = 0; cc < COLS; ++cc) {
+            e1[q][cc] = Real(t1[cc]);
+            e2[q][cc] = Real(t2[cc]);
+            if (PREC == kMIXED) e3[q][cc] = Real(t3[cc]);
+          }
         }
       }
       if (PREC == kMIXED && warp == 0 && lane < 6 && lead_in_range)
@@ -486,12 +573,21 @@ __global__ void __launch_bounds__(kMaxThreads) rk4_stage_kernel(const StageArgs 
       const int m = rl & (MS - 1);
       if (PREC == kFP64 || STAGE > 1) {
         // fp64: moments of u itself; mixed: of the increment (y's are running sums)
-        const Real s0 = (PREC == kFP64) ? u[K][0] : draw[0];
-        const Real s1 = (PREC == kFP64) ? u[K][1] : draw[1];
-        const Real s2 = (PREC == kFP64) ? u[K][2] : draw[2];
-        const Real s3 = (PREC == kFP64) ? u[K][3] : draw[3];
-        const Real t3 = s0 - s1;
-        const Real m6[6] = {w3 * t3, w3v * t3, w3 * s2, w3v * s2, wi * s3, wiv * s3};
+        Real m6[6] = {Real(0), Real(0), Real(0), Real(0), Real(0), Real(0)};
+#pragma unroll
+        for (int cc = 0; cc < COLS; ++cc) {
+          const Real s0 = (PREC == kFP64) ? u[K][0][cc] : draw[0][cc];
+          const Real s1 = (PREC == kFP64) ? u[K][1][cc] : draw[1][cc];
+          const Real s2 = (PREC == kFP64) ? u[K][2][cc] : draw[2][cc];
+          const Real s3 = (PREC == kFP64) ? u[K][3][cc] : draw[3][cc];
+          const Real t3 = s0 - s1;
+          m6[0] += w3[cc] * t3;
+          m6[1] += w3v[cc] * t3;
+          m6[2] += w3[cc] * s2;
+          m6[3] += w3v[cc] * s2;
+          m6[4] += wi[cc] * s3;
+          m6[5] += wiv[cc] * s3;
+        }
         const Real tot = warp_sum6_transposed(m6);
         const int k = (lane >> 2) & 7;
         if ((lane & 3) == 0 && k < 6) part[(m * kMaxWarps + warp) * 8 + k] = tot;
@@ -501,20 +597,26 @@ __global__ void __launch_bounds__(kMaxThreads) rk4_stage_kernel(const StageArgs 
     }
 
     // ---- center row c = i - lag
-    Real fcur[4] = {Real(0), Real(0), Real(0), Real(0)};
+    Real fcur[4][COLS];
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int cc = 0; cc < COLS; ++cc) fcur[q][cc] = Real(0);
     if (SCHEME == kWENO7 && rc >= -1 && c < z_end) {
       // flux F_{c+1/2} = v * WENO(u), upwind by the sign of v
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        Real r;
-        if (upwind_left)
-          r = weno7_face(u[W0][q], u[W1][q], u[W2][q], u[W3][q], u[W4][q], u[W5][q], u[W6][q],
-                         eps_v);
-        else
-          r = weno7_face(u[W7][q], u[W6][q], u[W5][q], u[W4][q], u[W3][q], u[W2][q], u[W1][q],
-                         eps_v);
-        fcur[q] = v * r;
-      }
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int cc = 0; cc < COLS; ++cc) {
+          Real r;
+          if (upwind_left[cc])
+            r = weno7_face(u[W0][q][cc], u[W1][q][cc], u[W2][q][cc], u[W3][q][cc], u[W4][q][cc],
+                           u[W5][q][cc], u[W6][q][cc], eps_v[cc]);
+          else
+            r = weno7_face(u[W7][q][cc], u[W6][q][cc], u[W5][q][cc], u[W4][q][cc], u[W3][q][cc],
+                           u[W2][q][cc], u[W1][q][cc], eps_v[cc]);
+          fcur[q][cc] = v[cc] * r;
+        }
     }
     if (center_in_range) {
       const int m = rc & (MS - 1);
@@ -525,66 +627,88 @@ __global__ void __launch_bounds__(kMaxThreads) rk4_stage_kernel(const StageArgs 
       const Acc* mf = momf + m * 8;
       const Real D30 = Real(mf[0]), D31 = Real(mf[1]), Dr0 = Real(mf[2]), Dr1 = Real(mf[3]),
                  Di0 = Real(mf[4]), Di1 = Real(mf[5]);
-      const Real dH = hd0 + mus * (D30 - v * D31);
-      const Real hr = hr0 + mus * (Dr0 - v * Dr1);
-      const Real hi = mu * (Di0 - v * Di1);
       constexpr int CC = (SCHEME == kFDKO) ? W2 : W3;  // the center row in the window
-      const Real ua = u[CC][0], ub = u[CC][1], ucr = u[CC][2], uci = u[CC][3];
-      const Real amb = ua - ub;
-      Real kk[4];
-      // -i [H, rho] for 2x2 Hermitian matrices, Eq. (eom)
-      const Real adot = Real(2) * (hi * ucr - hr * uci);
-      kk[0] = adot;
-      kk[1] = -adot;
-      kk[2] = dH * uci - amb * hi;
-      kk[3] = -dH * ucr + amb * hr;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        Real adv;
-        if (SCHEME == kFDKO) {
-          const Real um2 = u[W0][q], um1 = u[W1][q], u0 = u[W2][q], up1 = u[W3][q],
-                     up2 = u[W4][q];
-          const Real fd = Real(8) * (up1 - um1) - (up2 - um2);
-          const Real ko = (um2 + up2) - Real(4) * (um1 + up1) + Real(6) * u0;
-          adv = c_fd * fd + c_ko * ko;
-        } else {
-          adv = -(fcur[q] - fprev[q]) * inv_dz;
-        }
-        kk[q] += adv;
-      }
       const int64_t rowoff = c * nv;
+      Real kk[4][COLS];
+#pragma unroll
+      for (int cc = 0; cc < COLS; ++cc) {
+        const Real dH = hd0 + mus * (D30 - v[cc] * D31);
+        const Real hr = hr0 + mus * (Dr0 - v[cc] * Dr1);
+        const Real hi = mu * (Di0 - v[cc] * Di1);
+        const Real ua = u[CC][0][cc], ub = u[CC][1][cc], ucr = u[CC][2][cc], uci = u[CC][3][cc];
+        const Real amb = ua - ub;
+        // -i [H, rho] for 2x2 Hermitian matrices, Eq. (eom)
+        const Real adot = Real(2) * (hi * ucr - hr * uci);
+        kk[0][cc] = adot;
+        kk[1][cc] = -adot;
+        kk[2][cc] = dH * uci - amb * hi;
+        kk[3][cc] = -dH * ucr + amb * hr;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          Real adv;
+          if (SCHEME == kFDKO) {
+            const Real um2 = u[W0][q][cc], um1 = u[W1][q][cc], u0 = u[W2][q][cc],
+                       up1 = u[W3][q][cc], up2 = u[W4][q][cc];
+            const Real fd = Real(8) * (up1 - um1) - (up2 - um2);
+            const Real ko = (um2 + up2) - Real(4) * (um1 + up1) + Real(6) * u0;
+            adv = c_fd[cc] * fd + c_ko * ko;
+          } else {
+            adv = -(fcur[q][cc] - fprev[q][cc]) * inv_dz;
+          }
+          kk[q][cc] += adv;
+        }
+      }
       if (STAGE < 4) {
         const Real f = (STAGE == 3) ? dt : Real(0.5) * dt;
         if (active) {
 #pragma unroll
-          for (int q = 0; q < 4; ++q) dout[rowoff + (int64_t)q * plane] = Delta(f * kk[q]);
+          for (int q = 0; q < 4; ++q) {
+            Delta o[COLS];
+#pragma unroll
+            for (int cc = 0; cc < COLS; ++cc) o[cc] = Delta(f * kk[q][cc]);
+            vstore(dout + rowoff + (int64_t)q * plane, o);
+          }
         }
       } else {
-        Real incr[4];
+        Real incr[4][COLS];
         bool bad = false;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          Real d3;
-          if (PREC == kFP64)
-            d3 = Real(double(u[CC][q]) - yc[q]);  // u = y + delta_3 at the center
-          else
-            d3 = e3[q];
-          incr[q] = (e1[q] + Real(2) * e2[q] + d3) * Real(1.0 / 3.0) +
-                    (dt * Real(1.0 / 6.0)) * kk[q];
-          const double ynew =
-              yc[q] + (PREC == kFP64 ? double(incr[q]) : f2d_int(float(incr[q])));
-          bad |= !is_finite_bits(ynew);
+          double yn[COLS];
+          float y32n[COLS];
+#pragma unroll
+          for (int cc = 0; cc < COLS; ++cc) {
+            Real d3;
+            if (PREC == kFP64)
+              d3 = Real(double(u[CC][q][cc]) - yc[q][cc]);  // u = y + delta_3 at the center
+            else
+              d3 = e3[q][cc];
+            incr[q][cc] = (e1[q][cc] + Real(2) * e2[q][cc] + d3) * Real(1.0 / 3.0) +
+                          (dt * Real(1.0 / 6.0)) * kk[q][cc];
+            yn[cc] = yc[q][cc] +
+                     (PREC == kFP64 ? double(incr[q][cc]) : f2d_int(float(incr[q][cc])));
+            bad |= !is_finite_bits(yn[cc]);
+            if (PREC == kMIXED) y32n[cc] = d2f_rn_int(yn[cc]);
+          }
           if (active) {
-            yout[rowoff + (int64_t)q * plane] = ynew;
-            if (PREC == kMIXED) y32out[rowoff + (int64_t)q * plane] = d2f_rn_int(ynew);
+            vstore(yout + rowoff + (int64_t)q * plane, yn);
+            if (PREC == kMIXED) vstore(y32out + rowoff + (int64_t)q * plane, y32n);
           }
         }
         nonfinite |= bad;
         if (PREC == kMIXED) {
           // float moments of the increment advance the FP64 running moments of y
-          const Real t3 = incr[0] - incr[1];
-          const Real m6[6] = {w3 * t3, w3v * t3, w3 * incr[2], w3v * incr[2], wi * incr[3],
-                              wiv * incr[3]};
+          Real m6[6] = {Real(0), Real(0), Real(0), Real(0), Real(0), Real(0)};
+#pragma unroll
+          for (int cc = 0; cc < COLS; ++cc) {
+            const Real t3 = incr[0][cc] - incr[1][cc];
+            m6[0] += w3[cc] * t3;
+            m6[1] += w3v[cc] * t3;
+            m6[2] += w3[cc] * incr[2][cc];
+            m6[3] += w3v[cc] * incr[2][cc];
+            m6[4] += wi[cc] * incr[3][cc];
+            m6[5] += wiv[cc] * incr[3][cc];
+          }
           const Real tot = warp_sum6_transposed(m6);
           const int k = (lane >> 2) & 7;
           if ((lane & 3) == 0 && k < 6) partdy[(m * kMaxWarps + warp) * 8 + k] = tot;
@@ -595,7 +719,9 @@ __global__ void __launch_bounds__(kMaxThreads) rk4_stage_kernel(const StageArgs 
     }
     if (SCHEME == kWENO7) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) fprev[q] = fcur[q];
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int cc = 0; cc < COLS; ++cc) fprev[q][cc] = fcur[q][cc];
     }
   };
 
