@@ -182,6 +182,41 @@ const char* cosenu_last_error(cosenu_t h);
 /* Kernel launches the library has issued in this process (all handles). */
 uint64_t cosenu_kernel_launches(void);
 
+/* Conserved-quantity diagnostics without any device allocation.  (The paper has
+ * no counterpart: this entry point exists for callers of this library.)
+ *
+ * Same quantities as cosenu_conserved, for a state the caller holds in device
+ * memory: y_dev is the [2][4][nz][nv] double state (layout above) on an nz x nv
+ * grid of length L, theta the vacuum mixing angle used for M_vac, and out_dev
+ * a caller-owned device buffer of 8 doubles that receives
+ *   tr_nu, tr_nubar, M[0], M[1], M[2], M_vac, dP_max, dP_mean.
+ * The work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
+ * stream) and the call returns without waiting.
+ *
+ * Who needs it: code that must not call cudaMalloc -- for example a caller that
+ * records its work into a CUDA graph with stream capture (allocation is not
+ * allowed while capturing), or a process whose device memory is already fully
+ * handed to another allocator (a framework's caching pool, a serving budget) --
+ * and code that cannot afford the synchronisation an allocation may imply.
+ * This function calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ * Scratch: the per-block partial sums live in one static device array of the
+ * library (1 MiB, held on every GPU that loads the library until the process
+ * exits).  Hence:
+ *   - the grid may have at most 2^28 (z, v) cells (nz * nv <= 268435456);
+ *     larger grids are rejected with COSENU_EINVAL and a message;
+ *   - the first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress, with that device current); make that first call
+ *     before any stream capture;
+ *   - every call on a device shares the array: calls whose work overlaps on the
+ *     GPU (different streams without ordering) race and give wrong results.
+ *     Each call writes every partial it reads, so no clearing is needed between
+ *     calls.
+ * Returns 0, COSENU_EINVAL (bad argument, grid too large) or COSENU_ECUDA; the
+ * message is in cosenu_last_error(NULL). */
+int cosenu_conserved_noalloc(const double* y_dev, int64_t nz, int32_t nv, double L, double theta,
+                             double* out_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,7 +28,7 @@ EXPORTS = (
     "cosenu_step",
     "cosenu_sync", "cosenu_moments", "cosenu_conserved", "cosenu_set_stage_timing",
     "cosenu_stage_times", "cosenu_steps_taken",
-    "cosenu_last_error", "cosenu_kernel_launches",
+    "cosenu_last_error", "cosenu_kernel_launches", "cosenu_conserved_noalloc",
 )
 
 
@@ -86,6 +86,8 @@ def load(path: str = LIB_PATH):
         "cosenu_steps_taken": (i64, [vp]),
         "cosenu_last_error": (ctypes.c_char_p, [vp]),
         "cosenu_kernel_launches": (ctypes.c_uint64, []),
+        "cosenu_conserved_noalloc": (ctypes.c_int, [vp, i64, i32, ctypes.c_double, ctypes.c_double,
+                                                    vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -213,6 +215,15 @@ def cosenu_last_error(h=None):
 
 def cosenu_kernel_launches():
     return int(load().cosenu_kernel_launches())
+
+
+def cosenu_conserved_noalloc(y_dev_ptr, nz, nv, L, theta, out_dev_ptr, stream_handle=0):
+    """Enqueue the allocation-free diagnostics of a device state into a caller-owned
+    device buffer of 8 doubles (see include/cosenu.h)."""
+    rc = load().cosenu_conserved_noalloc(ctypes.c_void_p(int(y_dev_ptr)), int(nz), int(nv),
+                                         float(L), float(theta), ctypes.c_void_p(int(out_dev_ptr)),
+                                         ctypes.c_void_p(int(stream_handle or 0)))
+    return _check(None, rc)
 
 
 # ---------------------------------------------------------------- owner object

@@ -71,6 +71,11 @@ Layout make_layout(int64_t nz, int32_t nv, int precision) {
 
 }  // namespace
 
+namespace cosenu {
+void set_thread_error(const std::string& msg) { tl_error = msg; }
+void count_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+}  // namespace cosenu
+
 struct cosenu_s {
   int64_t nz = 0;
   int32_t nv = 0;
