@@ -432,3 +432,58 @@ def test_fast_instability_growth_rate(oracle):
     gamma_d = dispersion_growth(nv, keff, fid["alpha"], fid["sigma_nu"], fid["sigma_nubar"]) + ko_damp
     assert slope == pytest.approx(gamma_d, rel=0.02)
     assert np.max(np.abs(u[:, 2:])) < 1e-3  # still linear: |rho_ex| below 1e-3
+
+
+# --------------------------------------------------------------------------- diagnostics
+
+
+def test_conserved_closed_forms(oracle):
+    """z- and v-uniform states: every sum is (value) x sum(w dz) = (value) x 2L, and
+    |P|/P0 of a cell follows from the Bloch vector P = (2 Re, -2 Im, ee - xx)."""
+    nz, nv, L = 5, 8, 3.0
+    a, b, cr, ci = 0.7, 0.2, 0.1, -0.15
+    ab, bb, cbr, cbi = 0.4, 0.3, -0.05, 0.2
+    u = np.zeros((2, 4, nz, nv))
+    u[0, 0], u[0, 1], u[0, 2], u[0, 3] = a, b, cr, ci
+    u[1, 0], u[1, 1], u[1, 2], u[1, 3] = ab, bb, cbr, cbi
+    th = 0.35
+    c = oracle.conserved(oracle.params(nz, nv, L, theta=th), u)
+    assert c["tr_nu"] == pytest.approx((a + b) * 2 * L, rel=1e-14)
+    assert c["tr_nubar"] == pytest.approx((ab + bb) * 2 * L, rel=1e-14)
+    M = np.array([2 * (cr - cbr), -2 * (ci + cbi), (a - b) - (ab - bb)]) * 2 * L
+    assert np.allclose(c["M"], M, rtol=1e-14, atol=1e-15)
+    assert c["M_vac"] == pytest.approx(math.sin(2 * th) * M[0] - math.cos(2 * th) * M[2], abs=1e-14)
+    dp_nu = abs(math.sqrt((a - b) ** 2 + 4 * (cr * cr + ci * ci)) / (a + b) - 1)
+    dp_nb = abs(math.sqrt((ab - bb) ** 2 + 4 * (cbr * cbr + cbi * cbi)) / (ab + bb) - 1)
+    assert c["dP_max"] == pytest.approx(max(dp_nu, dp_nb), rel=1e-13)
+    assert c["dP_mean"] == pytest.approx(dp_nu, rel=1e-13)
+    # a pure state has |P| = P0
+    p = np.zeros((2, 4, nz, nv))
+    p[:, 0] = 0.5 * (1 + math.sqrt(1 - 0.3 ** 2))
+    p[:, 1] = 0.5 * (1 - math.sqrt(1 - 0.3 ** 2))
+    p[:, 2] = 0.15
+    assert oracle.conserved(oracle.params(nz, nv, L), p)["dP_max"] < 1e-15
+
+
+def test_moments_closed_forms(oracle):
+    """zavg of cos(2 pi z / nz) + const is const; with S_ee - S_xx = 1 + v the midpoint sums
+    give D3_0 = 2 and D3_1 = sum dv v^2 = 2/3 - dv^2/6 (midpoint rule error of v^2)."""
+    nz, nv = 8, 16
+    z = np.arange(nz)
+    v, _ = oracle.vgrid(nv)
+    u = np.zeros((2, 4, nz, nv))
+    u[0, 0] = (1 + v)[None, :] + np.cos(2 * np.pi * z / nz)[:, None]
+    u[0, 1] = np.cos(2 * np.pi * z / nz)[:, None]
+    u[1, 2] = 0.25
+    u[0, 3] = 0.5 * v[None, :]
+    zavg, vmom = oracle.moments(oracle.params(nz, nv, 1.0), u)
+    assert np.allclose(zavg[0, 0], 1 + v, atol=1e-15)
+    assert np.allclose(zavg[0, 1], 0.0, atol=1e-15)
+    assert np.allclose(zavg[1, 2], 0.25, atol=1e-16)
+    dv = 2.0 / nv
+    assert np.allclose(vmom[:, 0], 2.0, atol=1e-14)
+    assert np.allclose(vmom[:, 1], 2.0 / 3.0 - dv * dv / 6.0, atol=1e-14)
+    assert np.allclose(vmom[:, 2], -0.25 * 2.0, atol=1e-15)    # Dr = sum dv (cr - cbr)
+    assert np.allclose(vmom[:, 3], 0.0, atol=1e-15)
+    assert np.allclose(vmom[:, 4], 0.0, atol=1e-15)            # Di_0 = sum dv 0.5 v = 0
+    assert np.allclose(vmom[:, 5], 0.5 * (2.0 / 3.0 - dv * dv / 6.0), atol=1e-14)
