@@ -43,14 +43,17 @@ MU, ALPHA, SIG_NU, SIG_NUBAR, EPS0, SEED = 10.0, 0.9, 0.6, 0.5, 1e-6, 12866
 WORKLOAD = ("roofline run: nz=2^20, nv=256, z in [-25600,25600), dt=0.4 dz, mu=10, omega=0, "
             "alpha=0.9, sigma=(0.6,0.5), random-phase seed 1e-6")
 
-# Algorithmic HBM bytes per real component per launch of each RK4 stage.
+# Algorithmic HBM bytes per real component per launch of each kernel of an RK4
+# step (k = 1..4 the fused stage kernels, k = 5 the mixed path's increment kernel).
 # fp64 (all arrays double): stage 1 reads y, writes d1; stage 2 reads y, d1,
 #   writes d2; stage 3 reads y, d2, writes d3; stage 4 reads y, d3, d1, d2 and
-#   writes y.
+#   writes the new y.
 # mixed (state y double plus its float copy y32; increments float): stages 1-3
-#   read y32 instead of y; stage 4 reads y32, d3 (window), y, d1, d2 (center)
-#   and writes y and y32.
-STAGE_BYTES = {"fp64": (16, 24, 24, 40), "mixed": (8, 12, 12, 36)}
+#   read y32 instead of y; stage 4 reads y32, d3 (window), d1, d2 (center) and
+#   writes the float increment dy; the increment kernel reads y, dy and writes
+#   y, y32.
+STAGE_BYTES = {"fp64": (16, 24, 24, 40, 0), "mixed": (8, 12, 12, 20, 24)}
+KERNEL_NAMES = ("stage 1", "stage 2", "stage 3", "stage 4", "increment")
 # Algorithmic FP64 flops per cell (4 reals) per launch of the fp64 stages
 # (moments, Hamiltonian, commutator, stencil, RK axpy; FMA = 2 flops).
 FP64_FLOPS_PER_CELL = {"fdko": (98, 106, 106, 138), "weno7": (482, 490, 490, 522)}
@@ -234,15 +237,15 @@ def run_reference(args, world, rank):
 def stage_roofline(stage_ms, stage_n, prec, scheme, hbm_peak):
     out = []
     reals = 8 * NZ * NV
-    for s in range(4):
+    for s in range(5):
         if stage_n[s] == 0:
             continue
         avg_ms = stage_ms[s] / stage_n[s]
         byts = STAGE_BYTES[prec][s] * reals
         gbs = byts / (avg_ms * 1e-3) / 1e9
-        rec = {"stage": s + 1, "avg_ms": avg_ms, "alg_bytes": byts, "GB/s": gbs,
-               "hbm_frac": gbs / hbm_peak, "total_ms": stage_ms[s]}
-        if prec == "fp64":
+        rec = {"kernel": KERNEL_NAMES[s], "stage": s + 1, "avg_ms": avg_ms, "alg_bytes": byts,
+               "GB/s": gbs, "hbm_frac": gbs / hbm_peak, "total_ms": stage_ms[s]}
+        if prec == "fp64" and s < 4:
             fl = FP64_FLOPS_PER_CELL[scheme][s] * 2 * NZ * NV
             rec["fp64_tflops"] = fl / (avg_ms * 1e-3) / 1e12
             rec["fp64_alu_frac"] = rec["fp64_tflops"] / FP64_PEAK_TFLOPS
@@ -331,7 +334,8 @@ def run_ours(args, world, rank, local):
     traffic = ncu_traffic(scheme, prec, dom["stage"])
     roofline = {"bound": "hbm", "achieved": dom["GB/s"], "peak": hbm_peak, "unit": "GB/s",
                 "frac": dom["hbm_frac"], "traffic": traffic,
-                "kernel": f"rk4_stage_kernel<{scheme},{prec},stage {dom['stage']}>",
+                "kernel": (f"rk4_stage_kernel<{scheme},{prec},stage {dom['stage']}>"
+                           if dom["stage"] <= 4 else "apply_increment_kernel"),
                 "peak_kind": f"{peak_kind} (copy)", "stages": stages,
                 "step_frac": (sum(STAGE_BYTES[prec]) * 8 * NZ * NV / (ms_step * 1e-3) / 1e9)
                 / hbm_peak}

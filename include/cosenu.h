@@ -164,12 +164,14 @@ int cosenu_moments(cosenu_t h, double* zavg, double* vmom);
 /* Diagnostics of the current state (waits). */
 int cosenu_conserved(cosenu_t h, cosenu_conserved_t* out);
 
-/* Stage timing.  With on != 0, every stage launch of later cosenu_step calls is
- * bracketed by CUDA events on the handle's stream (and steps are launched
+/* Kernel timing.  With on != 0, every kernel launch of later cosenu_step calls
+ * is bracketed by CUDA events on the handle's stream (and steps are launched
  * directly rather than replayed from a graph).  cosenu_stage_times waits for
- * the stream and returns, per RK4 stage s = 1..4, the summed device time in
- * milliseconds ms[s-1] and the number of timed launches n[s-1] since the last
- * call (either pointer may be NULL), then clears the sums. */
+ * the stream and returns, per kernel k of an RK4 step (k = 1..4: the fused
+ * stage kernels; k = 5: the mixed path's state-increment kernel, zero launches
+ * in the FP64 path), the summed device time in milliseconds ms[k-1] and the
+ * number of timed launches n[k-1] since the last call (arrays of 5; either
+ * pointer may be NULL), then clears the sums. */
 int cosenu_set_stage_timing(cosenu_t h, int on);
 int cosenu_stage_times(cosenu_t h, double* ms, int64_t* n);
 

@@ -198,9 +198,10 @@ def cosenu_set_stage_timing(h, on=True):
 
 
 def cosenu_stage_times(h):
-    """(ms[4], launches[4]) summed per RK4 stage since the last call."""
-    ms = np.zeros(4)
-    n = (ctypes.c_int64 * 4)()
+    """(ms[5], launches[5]) summed per kernel of the step (stages 1-4, increment) since
+    the last call."""
+    ms = np.zeros(5)
+    n = (ctypes.c_int64 * 5)()
     _check(h, load().cosenu_stage_times(h, _dptr(ms), n))
     return ms, np.array(n[:], dtype=np.int64)
 

@@ -1,10 +1,12 @@
 // C ABI of the COSEnu GB300 engine (declared in include/cosenu.h).
 //
-// A handle owns one solver: the state in two ping-pong buffers (stage 4 reads
-// the old state with a halo while writing the new one), the three RK4 stage
-// increments, the per-z running moments of the mixed path, and a small
-// reduction scratch area.  cosenu_step() enqueues four fused stage kernels per
-// RK4 step on the handle's stream; pairs of steps are replayed from a CUDA
+// A handle owns one solver: the state (FP64 path: two ping-pong buffers, since
+// stage 4 reads the old state with a halo while writing the new one; mixed
+// path: one buffer plus its float copy, updated in place by the increment
+// kernel), the three RK4 stage increments, the per-z running moments of the
+// mixed path, and a small reduction scratch area.  cosenu_step() enqueues the
+// four fused stage kernels of each RK4 step (plus the increment kernel in the
+// mixed path) on the handle's stream; pairs of steps are replayed from a CUDA
 // graph when the stream allows capture.
 #include <atomic>
 #include <cmath>
@@ -31,7 +33,7 @@ constexpr int kSmemLimit = 232448;
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 struct StageCfg {
-  int grid = 0, block = 0, ring = 0, slot_bytes = 0;
+  int grid = 0, block = 0, ring = 0, rows_per_slot = 1, slot_bytes = 0;
   int64_t rows = 0;
   size_t smem = 0;
 };
@@ -53,10 +55,11 @@ Layout make_layout(int64_t nz, int32_t nv, int precision) {
   const size_t dsz = precision == COSENU_FP64 ? sizeof(double) : sizeof(float);
   size_t off = 0;
   L.y0 = off; off = align_up(off + n * sizeof(double));
-  L.y1 = off; off = align_up(off + n * sizeof(double));
-  const size_t n32 = precision == COSENU_MIXED ? n : 0;  // float copies of y (mixed)
+  const size_t n1 = precision == COSENU_FP64 ? n : 0;    // second state buffer (fp64)
+  L.y1 = off; off = align_up(off + n1 * sizeof(double));
+  const size_t n32 = precision == COSENU_MIXED ? n : 0;  // float copy of y (mixed)
   L.y32a = off; off = align_up(off + n32 * sizeof(float));
-  L.y32b = off; off = align_up(off + n32 * sizeof(float));
+  L.y32b = off;
   L.d1 = off; off = align_up(off + n * dsz);
   L.d2 = off; off = align_up(off + n * dsz);
   L.d3 = off; off = align_up(off + n * dsz);
@@ -88,16 +91,17 @@ struct cosenu_s {
   unsigned char* ws = nullptr;
   Layout lay{};
   double* y[2] = {nullptr, nullptr};
-  float* y32[2] = {nullptr, nullptr};  // mixed: float copies of y[0], y[1]
+  float* y32[2] = {nullptr, nullptr};  // mixed: float copy of y[0]
   int ycur = 0;
   void* d[3] = {nullptr, nullptr, nullptr};
   double* my = nullptr;
   uint32_t* err = nullptr;
   StageCfg cfg[5];
+  int nsm = 0;
   cudaGraphExec_t graph = nullptr;  // two RK4 steps starting from y[0]
   bool timing = false;
   std::vector<cudaEvent_t> ev_free;                    // reusable events
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[5];  // per stage: (start, stop)
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[6];  // per kernel: (start, stop)
   int64_t steps = 0;
   std::string error;
 };
@@ -122,8 +126,20 @@ int cuda_fail(cosenu_t h, cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
   } while (0)
 
+// Every pointer a stage kernel dereferences must be set (a launch with a
+// missing buffer is refused instead of faulting on the device).
+bool stage_args_complete(const cosenu_s* h, int stage, const StageArgs& a) {
+  const bool mixed = h->precision == COSENU_MIXED;
+  if (!a.err || (mixed ? !a.y32_in || !a.my : !a.y_in)) return false;
+  if (stage > 1 && !a.d_in) return false;
+  if ((stage < 4 || mixed) && !a.d_out) return false;
+  if (stage == 4 && (!a.d1 || !a.d2 || (!mixed && !a.y_out))) return false;
+  return true;
+}
+
 cudaError_t launch_stage(cosenu_t h, int stage, const StageArgs& a) {
   const StageCfg& c = h->cfg[stage];
+  if (!stage_args_complete(h, stage, a)) return cudaErrorInvalidValue;
   cudaError_t e;
   if (h->scheme == COSENU_FDKO && h->precision == COSENU_FP64)
     e = launch_rk4_stage<kFDKO, kFP64>(stage, a, c.grid, c.block, c.smem, h->stream);
@@ -146,53 +162,90 @@ int max_blocks(cosenu_t h, int stage, int block, size_t smem) {
   return stage_max_blocks_per_sm<kWENO7, kMIXED>(stage, block, smem);
 }
 
-int cols_per_thread(cosenu_t h) {
+// Per-stage launch traits of the (scheme, precision) pair of a handle.
+struct StageTraits {
+  int cols, header;
+};
+
+template <int SCHEME, int PREC, int STAGE>
+StageTraits traits_of() {
+  return {cosenu::stage_cols<SCHEME, PREC, STAGE>(),
+          cosenu::stage_smem_header_bytes<SCHEME, PREC, STAGE>()};
+}
+
+template <int SCHEME, int PREC>
+StageTraits traits_for_stage(int stage) {
+  switch (stage) {
+    case 1: return traits_of<SCHEME, PREC, 1>();
+    case 2: return traits_of<SCHEME, PREC, 2>();
+    case 3: return traits_of<SCHEME, PREC, 3>();
+    default: return traits_of<SCHEME, PREC, 4>();
+  }
+}
+
+StageTraits stage_traits(cosenu_t h, int stage) {
   if (h->scheme == COSENU_FDKO)
-    return h->precision == COSENU_FP64 ? cosenu::stage_cols<kFDKO, kFP64>()
-                                       : cosenu::stage_cols<kFDKO, kMIXED>();
-  return h->precision == COSENU_FP64 ? cosenu::stage_cols<kWENO7, kFP64>()
-                                     : cosenu::stage_cols<kWENO7, kMIXED>();
+    return h->precision == COSENU_FP64 ? traits_for_stage<kFDKO, kFP64>(stage)
+                                       : traits_for_stage<kFDKO, kMIXED>(stage);
+  return h->precision == COSENU_FP64 ? traits_for_stage<kWENO7, kFP64>(stage)
+                                     : traits_for_stage<kWENO7, kMIXED>(stage);
 }
 
-int slot_bytes(cosenu_t h, int stage) {
-  return h->precision == COSENU_FP64 ? slot_layout<kFP64>(h->nv, stage).bytes
-                                     : slot_layout<kMIXED>(h->nv, stage).bytes;
+int slot_bytes(cosenu_t h, int stage, int rows) {
+  return h->precision == COSENU_FP64 ? slot_layout<kFP64>(h->nv, stage, rows).bytes
+                                     : slot_layout<kMIXED>(h->nv, stage, rows).bytes;
 }
 
-// Launch shape of each stage: one thread per (species, v) column; the ring
-// depth that gives the most resident CTAs per SM (then the deepest ring);
-// a persistent grid of at most (SMs x resident CTAs) CTAs with contiguous z
-// ranges of at least kMinRowsPerCta rows.
+// Launch shape of each stage.  One thread per (species, v) column pair (FD4+KO)
+// or column (WENO7), plus a producer and a reducer warp.  The ring: R z rows
+// per slot (one bulk copy per component plane moves R rows) and D >= 2 slots;
+// among the (R, D) that fit, take the largest copy size times resident CTAs
+// (up to 4 KB), then the most resident CTAs, then the deepest ring.  Persistent
+// grid: at most SMs x resident CTAs, contiguous z ranges of at least
+// kMinRowsPerCta rows.
 int configure(cosenu_t h) {
   int dev = 0, nsm = 0;
   CK(h, cudaGetDevice(&dev));
   CK(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  const int header = h->precision == COSENU_FP64 ? stage_smem_header_bytes<kFP64>()
-                                                 : stage_smem_header_bytes<kMIXED>();
+  h->nsm = nsm;
   for (int s = 1; s <= 4; ++s) {
+    const StageTraits tr = stage_traits(h, s);
     StageCfg c;
-    // consumer warps (cols adjacent columns per thread) + producer + reducer warps
-    const int cols = cols_per_thread(h);
-    c.block = ((2 * h->nv + 32 * cols - 1) / (32 * cols)) * 32 + 64;
-    c.slot_bytes = slot_bytes(h, s);
-    int best_occ = 0, best_d = 0;
-    for (int D = 2; D <= kMaxRing; ++D) {
-      const size_t smem = (size_t)header + (size_t)D * c.slot_bytes;
-      if (smem > (size_t)kSmemLimit) break;
-      const int occ = max_blocks(h, s, c.block, smem);
-      if (occ < 0) return fail(h, COSENU_ECUDA, "occupancy query failed");
-      if (occ <= 0) continue;
-      // prefer more resident CTAs while the ring stays at least 3 deep
-      const bool better = (occ > best_occ && (D >= 3 || best_d < 3)) ||
-                          (occ == best_occ && D > best_d) || best_d == 0;
-      if (better) {
-        best_occ = occ;
-        best_d = D;
+    c.block = ((2 * h->nv + 32 * tr.cols - 1) / (32 * tr.cols)) * 32 + 64;
+    int64_t best_score = -1;
+    int best_occ = 0, best_d = 0, best_r = 0;
+    for (int R = 1; R <= 32; R *= 2) {
+      const int slot = slot_bytes(h, s, R);
+      for (int D = 2; D <= kMaxRing; ++D) {
+        // Consumer warps drift apart by at most D * R rows; the moment-slot
+        // barriers stay unambiguous only while that is <= kMomSlots - 2.
+        if (D * R > kMomSlots - 2) break;
+        const size_t smem = (size_t)tr.header + (size_t)D * slot;
+        if (smem > (size_t)kSmemLimit) break;
+        const int occ = max_blocks(h, s, c.block, smem);
+        if (occ < 0) return fail(h, COSENU_ECUDA, "occupancy query failed");
+        if (occ <= 0) continue;
+        // Bandwidth depends mostly on the contiguous bytes each bulk copy moves
+        // per component plane (R rows of nv floats) times the resident CTAs:
+        // ~1 KB per copy reaches about 40% of HBM peak, 2 KB with two CTAs or
+        // 4 KB with one about 95% (measured on GB300).
+        const int64_t score = std::min<int64_t>((int64_t)R * h->nv * 4 * occ, 4096);
+        const bool better = score > best_score ||
+                            (score == best_score &&
+                             (occ > best_occ || (occ == best_occ && D > best_d)));
+        if (better) {
+          best_score = score;
+          best_occ = occ;
+          best_d = D;
+          best_r = R;
+        }
       }
     }
     if (best_d == 0) return fail(h, COSENU_EINVAL, "grid row does not fit in shared memory");
     c.ring = best_d;
-    c.smem = (size_t)header + (size_t)best_d * c.slot_bytes;
+    c.rows_per_slot = best_r;
+    c.slot_bytes = slot_bytes(h, s, best_r);
+    c.smem = (size_t)tr.header + (size_t)best_d * c.slot_bytes;
     const int64_t max_grid = (int64_t)nsm * best_occ;
     int64_t grid = (h->nz + kMinRowsPerCta - 1) / kMinRowsPerCta;
     if (grid > max_grid) grid = max_grid;
@@ -212,6 +265,7 @@ StageArgs stage_args(cosenu_t h, int stage, int ycur) {
   a.ncols = 2 * h->nv;
   a.rows_per_cta = h->cfg[stage].rows;
   a.ring = h->cfg[stage].ring;
+  a.rows_per_slot = h->cfg[stage].rows_per_slot;
   a.slot_bytes = h->cfg[stage].slot_bytes;
   a.inv_dz = (double)h->nz / h->L;
   a.dt = h->p.dt;
@@ -223,15 +277,15 @@ StageArgs stage_args(cosenu_t h, int stage, int ycur) {
   a.weno_eps = h->p.weno_eps;
   a.y_in = h->y[ycur];
   a.y_out = h->y[ycur ^ 1];
-  a.y32_in = h->y32[ycur];
-  a.y32_out = h->y32[ycur ^ 1];
+  a.y32_in = h->y32[0];
   a.my = h->my;
   a.err = h->err;
   switch (stage) {
     case 1: a.d_out = h->d[0]; break;
     case 2: a.d_in = h->d[0]; a.d_out = h->d[1]; break;
     case 3: a.d_in = h->d[1]; a.d_out = h->d[2]; break;
-    default: a.d_in = h->d[2]; a.d1 = h->d[0]; a.d2 = h->d[1]; break;
+    default:  // mixed: the increment dy overwrites delta_1 (read by this CTA only)
+      a.d_in = h->d[2]; a.d1 = h->d[0]; a.d2 = h->d[1]; a.d_out = h->d[0]; break;
   }
   return a;
 }
@@ -245,8 +299,21 @@ cudaError_t take_event(cosenu_t h, cudaEvent_t* out) {
   return cudaEventCreate(out);
 }
 
+cudaError_t launch_apply(cosenu_t h) {
+  const int64_t n = 8 * h->nz * (int64_t)h->nv;
+  const int64_t blocks = std::min<int64_t>((n / 4 + 255) / 256, (int64_t)h->nsm * 8);
+  apply_increment_kernel<<<(int)blocks, 256, 0, h->stream>>>(
+      h->y[0], h->y32[0], static_cast<const float*>(h->d[0]), n, h->err);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
+  return e;
+}
+
+// One RK4 step: stages 1-4, then (mixed) the increment kernel.  Kernel k of the
+// step (1..4 stages, 5 increment) is bracketed by events when timing is on.
 cudaError_t enqueue_step(cosenu_t h, int ycur) {
-  for (int s = 1; s <= 4; ++s) {
+  const int nk = h->precision == COSENU_MIXED ? 5 : 4;
+  for (int s = 1; s <= nk; ++s) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (h->timing) {
       cudaError_t e = take_event(h, &e0);
@@ -254,7 +321,7 @@ cudaError_t enqueue_step(cosenu_t h, int ycur) {
       if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
       if (e != cudaSuccess) return e;
     }
-    cudaError_t e = launch_stage(h, s, stage_args(h, s, ycur));
+    cudaError_t e = s <= 4 ? launch_stage(h, s, stage_args(h, s, ycur)) : launch_apply(h);
     if (e != cudaSuccess) return e;
     if (h->timing) {
       e = cudaEventRecord(e1, h->stream);
@@ -264,6 +331,9 @@ cudaError_t enqueue_step(cosenu_t h, int ycur) {
   }
   return cudaSuccess;
 }
+
+// The state buffer that follows a step from `ycur` (the mixed path updates in place).
+int next_y(cosenu_t h, int ycur) { return h->precision == COSENU_FP64 ? ycur ^ 1 : ycur; }
 
 void drop_graph(cosenu_t h) {
   if (h->graph) cudaGraphExecDestroy(h->graph);
@@ -277,7 +347,7 @@ int build_graph(cosenu_t h) {
   CK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
   const uint64_t before = g_launches.load();
   cudaError_t e = enqueue_step(h, 0);
-  if (e == cudaSuccess) e = enqueue_step(h, 1);
+  if (e == cudaSuccess) e = enqueue_step(h, next_y(h, 0));
   cudaError_t e2 = cudaStreamEndCapture(h->stream, &g);
   g_launches.store(before);  // captured launches run later, counted per replay
   if (e != cudaSuccess) {
@@ -348,11 +418,10 @@ cosenu_t create_common(int64_t nz, int32_t nv, double L, int scheme, int precisi
   if (e != cudaSuccess) return bail(std::string("stream: ") + cudaGetErrorString(e), COSENU_ECUDA);
   h->own_stream = true;
   h->y[0] = reinterpret_cast<double*>(h->ws + h->lay.y0);
-  h->y[1] = reinterpret_cast<double*>(h->ws + h->lay.y1);
-  if (precision == COSENU_MIXED) {
+  if (precision == COSENU_FP64)
+    h->y[1] = reinterpret_cast<double*>(h->ws + h->lay.y1);
+  else
     h->y32[0] = reinterpret_cast<float*>(h->ws + h->lay.y32a);
-    h->y32[1] = reinterpret_cast<float*>(h->ws + h->lay.y32b);
-  }
   h->d[0] = h->ws + h->lay.d1;
   h->d[1] = h->ws + h->lay.d2;
   h->d[2] = h->ws + h->lay.d3;
@@ -410,7 +479,7 @@ void cosenu_destroy(cosenu_t h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
   drop_graph(h);
-  for (int s = 1; s <= 4; ++s)
+  for (int s = 1; s <= 5; ++s)
     for (auto& pr : h->ev[s]) {
       cudaEventDestroy(pr.first);
       cudaEventDestroy(pr.second);
@@ -511,12 +580,12 @@ int cosenu_step(cosenu_t h, int64_t nsteps) {
     }
     for (; left >= 2; left -= 2) {
       CK(h, cudaGraphLaunch(h->graph, h->stream));
-      g_launches.fetch_add(8, std::memory_order_relaxed);
+      g_launches.fetch_add(h->precision == COSENU_MIXED ? 10 : 8, std::memory_order_relaxed);
     }
   }
   for (; left > 0; --left) {
     CK(h, enqueue_step(h, h->ycur));
-    h->ycur ^= 1;
+    h->ycur = next_y(h, h->ycur);
   }
   h->steps += nsteps;
   return COSENU_OK;
@@ -597,7 +666,7 @@ int cosenu_set_stage_timing(cosenu_t h, int on) {
 int cosenu_stage_times(cosenu_t h, double* ms, int64_t* n) {
   if (!h) return fail(h, COSENU_EINVAL, "NULL handle");
   CK(h, cudaStreamSynchronize(h->stream));
-  for (int s = 1; s <= 4; ++s) {
+  for (int s = 1; s <= 5; ++s) {
     double sum = 0.0;
     for (auto& pr : h->ev[s]) {
       float t = 0.0f;

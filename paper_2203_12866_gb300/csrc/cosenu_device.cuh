@@ -35,7 +35,8 @@ struct StageArgs {
   int32_t nv;
   int32_t ncols;          // 2 * nv active threads
   int64_t rows_per_cta;   // contiguous z rows owned by each CTA
-  int32_t ring;           // bulk-copy ring depth (rows in flight)
+  int32_t ring;           // bulk-copy ring depth (slots)
+  int32_t rows_per_slot;  // consecutive z rows per ring slot (one bulk copy per plane)
   int32_t slot_bytes;     // bytes of one ring slot
   double inv_dz;          // 1 / dz
   double dt;
@@ -45,13 +46,11 @@ struct StageArgs {
   double lambda;          // matter potential (nu: +, nubar: -)
   double ko_eps;
   double weno_eps;
-  const double* y_in;     // state at the start of the step (fp64: read with halo;
-                          // mixed: center rows of stage 4 only)
-  double* y_out;          // stage 4: state at the end of the step
-  const float* y32_in;    // mixed: float copy of y_in (read with halo)
-  float* y32_out;         // mixed, stage 4: float copy of y_out
+  const double* y_in;     // fp64: state at the start of the step (read with halo)
+  double* y_out;          // fp64, stage 4: state at the end of the step
+  const float* y32_in;    // mixed: float copy of the state (read with halo)
   const void* d_in;       // stage s > 1: delta_{s-1} (read with halo)
-  void* d_out;            // stages 1-3: delta_s
+  void* d_out;            // stages 1-3: delta_s; mixed stage 4: the increment dy
   const void* d1;         // stage 4: delta_1 (center rows only)
   const void* d2;         // stage 4: delta_2 (center rows only)
   double* my;             // mixed: running FP64 moments of y, [nz][8] (6 used)

@@ -56,6 +56,35 @@ __global__ void y32_from_y_kernel(const double* __restrict__ y, float* __restric
     y32[e] = d2f_rn_int(y[e]);
 }
 
+// Mixed path, end of an RK4 step: y <- y + dy in double (dy is the float
+// increment written by stage 4) and the float copy y32 <- round(y), in place,
+// element by element.  n = 8 nz nv (a multiple of 4).
+__global__ void __launch_bounds__(256) apply_increment_kernel(double* __restrict__ y,
+                                                               float* __restrict__ y32,
+                                                               const float* __restrict__ dy,
+                                                               int64_t n, uint32_t* err) {
+  bool bad = false;
+  const int64_t n4 = n >> 2;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const float4 d = reinterpret_cast<const float4*>(dy)[i];
+    double2 a = reinterpret_cast<double2*>(y)[2 * i];
+    double2 b = reinterpret_cast<double2*>(y)[2 * i + 1];
+    a.x += f2d_int(d.x);
+    a.y += f2d_int(d.y);
+    b.x += f2d_int(d.z);
+    b.y += f2d_int(d.w);
+    bad |= !(is_finite_bits(a.x) && is_finite_bits(a.y) && is_finite_bits(b.x) &&
+             is_finite_bits(b.y));
+    reinterpret_cast<double2*>(y)[2 * i] = a;
+    reinterpret_cast<double2*>(y)[2 * i + 1] = b;
+    reinterpret_cast<float4*>(y32)[i] =
+        make_float4(d2f_rn_int(a.x), d2f_rn_int(a.y), d2f_rn_int(b.x), d2f_rn_int(b.y));
+  }
+  if (__ballot_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, kErrNonFinite);
+}
+
+
 // Column sums over z: out[q][v] = (1/nz) sum_z y[q][z][v].  Block = (q, 32 v);
 // 8 warps split z, partial sums combined in a fixed order.
 __global__ void zavg_kernel(const double* __restrict__ y, int64_t nz, int nv,

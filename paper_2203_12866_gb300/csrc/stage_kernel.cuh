@@ -6,6 +6,10 @@
 //         - i [H(u_s), u_s]                                 (Eq. (eom), (ham))
 //   delta_1 = dt/2 k_1, delta_2 = dt/2 k_2, delta_3 = dt k_3,
 //   y <- y + (delta_1 + 2 delta_2 + delta_3) / 3 + dt/6 k_4   (classic RK4)
+// In the mixed path stage 4 writes the float increment
+//   dy = (delta_1 + 2 delta_2 + delta_3) / 3 + dt/6 k_4
+// (over delta_1, which only this CTA reads at those rows) and a separate
+// streaming kernel, apply_increment_kernel, performs y <- y + dy in double.
 //
 // Work decomposition.  A CTA owns a contiguous range of z rows and all 2 nv
 // (species, v) columns, and marches along z with three warp roles:
@@ -76,9 +80,15 @@ struct Scheme<kWENO7> {
 // shared by both columns.  One (WENO7): the reconstruction is arithmetic-heavy
 // and needs the latency hiding of twice as many warps (and its FP64 window
 // would not fit in the registers twice).
-template <int SCHEME, int PREC>
+template <int SCHEME, int PREC, int STAGE>
 __host__ __device__ constexpr int stage_cols() {
   return SCHEME == kWENO7 ? 1 : 2;
+}
+
+// Most consumer warps a stage kernel can have (256 v-columns per species).
+template <int SCHEME, int PREC, int STAGE>
+__host__ __device__ constexpr int stage_max_consumer_warps() {
+  return kMaxWarps / stage_cols<SCHEME, PREC, STAGE>();
 }
 
 template <typename T, int N>
@@ -107,62 +117,58 @@ __device__ __forceinline__ void vstore(T* p, const T (&in)[N]) {
   }
 }
 
-// Byte layout of one ring slot.  Window arrays belong to the leading row i,
-// center arrays (stage 4 only) to the row i - lag.
+// Byte layout of one ring slot.  A slot carries R consecutive z rows: for each
+// array, the R rows of component plane q are contiguous ([q][r][v]) because
+// they are contiguous in global memory, so one bulk copy moves R rows of a
+// plane.  Window arrays belong to the leading rows i, center arrays (stage 4
+// only) to the rows i - lag.
 struct SlotLayout {
-  int y_off, din_off, yc_off, d1c_off, d2c_off, d3c_off, my_off, bytes;
+  int y_off, din_off, yc_off, d1c_off, d2c_off, my_off, bytes;
 };
 
 template <int PREC>
-__host__ __device__ inline SlotLayout slot_layout(int nv, int stage) {
+__host__ __device__ inline SlotLayout slot_layout(int nv, int stage, int R) {
   using Delta = typename Prec<PREC>::Delta;
   using WinY = typename Prec<PREC>::WinY;
   SlotLayout L;
-  const int row_w = 8 * nv * (int)sizeof(WinY);
-  const int row_y = 8 * nv * (int)sizeof(double);
-  const int row_d = 8 * nv * (int)sizeof(Delta);
+  const int row_w = 8 * nv * (int)sizeof(WinY) * R;
+  const int row_y = 8 * nv * (int)sizeof(double) * R;
+  const int row_d = 8 * nv * (int)sizeof(Delta) * R;
   int off = 0;
   L.y_off = off;
   off += row_w;
   L.din_off = off;
   if (stage > 1) off += row_d;
   L.yc_off = off;
-  if (stage == 4) off += row_y;
+  if (stage == 4 && PREC == kFP64) off += row_y;
   L.d1c_off = off;
   if (stage == 4) off += row_d;
   L.d2c_off = off;
   if (stage == 4) off += row_d;
-  L.d3c_off = off;  // mixed: delta_3 of the center row (the window holds y + delta_3)
-  if (stage == 4 && PREC == kMIXED) off += row_d;
   L.my_off = off;
-  if (PREC == kMIXED) off += 8 * (int)sizeof(double);
+  if (PREC == kMIXED) off += 8 * (int)sizeof(double) * R;
   L.bytes = (off + 127) & ~127;
   return L;
 }
 
 // Shared memory besides the ring.  Acc is the type of the moment partials.
 //   mbarriers: full[kMaxRing] empty[kMaxRing] part[kMomSlots] mom[kMomSlots] dy[kMomSlots]
-//   flags (abort), partials [kMomSlots][kMaxWarps][8] Acc, dy partials (mixed
+//   flags (abort), partials [kMomSlots][NW consumer warps][8] Acc, dy partials (mixed
 //   only, same shape), finished moments [kMomSlots][8] Acc, running moments of
 //   y (mixed) [kMomSlots][8] double.
-template <int PREC>
+template <int PREC, int NW>
 struct SmemHeader {
   using Acc = typename Prec<PREC>::Real;
   static constexpr int kBars = 0;
   static constexpr int kNumBars = 2 * kMaxRing + 3 * kMomSlots;
   static constexpr int kFlags = kBars + kNumBars * 8;
   static constexpr int kPart = ((kFlags + 64) + 127) & ~127;
-  static constexpr int kPartBytes = kMomSlots * kMaxWarps * 8 * (int)sizeof(Acc);
+  static constexpr int kPartBytes = kMomSlots * NW * 8 * (int)sizeof(Acc);
   static constexpr int kPartDy = kPart + kPartBytes;
   static constexpr int kMomf = kPartDy + (PREC == kMIXED ? kPartBytes : 0);
   static constexpr int kMyRing = kMomf + kMomSlots * 8 * (int)sizeof(Acc);
   static constexpr int kBytes = ((kMyRing + kMomSlots * 8 * 8) + 127) & ~127;
 };
-
-template <int PREC>
-__host__ __device__ inline int stage_smem_header_bytes() {
-  return SmemHeader<PREC>::kBytes;
-}
 
 // Calls f(std::integral_constant<int, K>) for K = B .. E-1 (compile-time unrolled).
 template <int B, int E, typename F>
@@ -252,18 +258,25 @@ __device__ __forceinline__ float weno7_face(float fm3, float fm2, float fm1, flo
 
 // Largest CTA of a stage kernel: consumer warps for 256 v-columns per species,
 // plus the producer and reducer warps.
-template <int SCHEME, int PREC>
+template <int SCHEME, int PREC, int STAGE>
 __host__ __device__ constexpr int stage_max_threads() {
-  return (kMaxWarps / stage_cols<SCHEME, PREC>() + 2) * 32;
+  return (stage_max_consumer_warps<SCHEME, PREC, STAGE>() + 2) * 32;
+}
+
+// Shared memory of a stage kernel besides its ring slots.
+template <int SCHEME, int PREC, int STAGE>
+__host__ __device__ constexpr int stage_smem_header_bytes() {
+  return SmemHeader<PREC, stage_max_consumer_warps<SCHEME, PREC, STAGE>()>::kBytes;
 }
 
 template <int SCHEME, int PREC, int STAGE>
-__global__ void __launch_bounds__(stage_max_threads<SCHEME, PREC>())
+__global__ void __launch_bounds__(stage_max_threads<SCHEME, PREC, STAGE>())
     rk4_stage_kernel(const StageArgs a) {
   using Real = typename Prec<PREC>::Real;
   using Delta = typename Prec<PREC>::Delta;
   using Acc = Real;
-  using H = SmemHeader<PREC>;
+  constexpr int NW = stage_max_consumer_warps<SCHEME, PREC, STAGE>();
+  using H = SmemHeader<PREC, NW>;
   constexpr int LAG = Scheme<SCHEME>::kLag;
   constexpr int WIN = Scheme<SCHEME>::kWin;
   constexpr int LO = Scheme<SCHEME>::kLo;
@@ -272,8 +285,8 @@ __global__ void __launch_bounds__(stage_max_threads<SCHEME, PREC>())
 
   extern __shared__ __align__(128) unsigned char smem[];
   volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + H::kFlags);
-  Acc* part = reinterpret_cast<Acc*>(smem + H::kPart);      // [MS][kMaxWarps][8]
-  Acc* partdy = reinterpret_cast<Acc*>(smem + H::kPartDy);  // [MS][kMaxWarps][8]
+  Acc* part = reinterpret_cast<Acc*>(smem + H::kPart);      // [MS][NW][8]
+  Acc* partdy = reinterpret_cast<Acc*>(smem + H::kPartDy);  // [MS][NW][8]
   Acc* momf = reinterpret_cast<Acc*>(smem + H::kMomf);      // [MS][8]
   double* myring = reinterpret_cast<double*>(smem + H::kMyRing);  // [MS][8]
   unsigned char* ring = smem + H::kBytes;
@@ -281,11 +294,12 @@ __global__ void __launch_bounds__(stage_max_threads<SCHEME, PREC>())
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int warp = tid >> 5;
-  constexpr int COLS = stage_cols<SCHEME, PREC>();
+  constexpr int COLS = stage_cols<SCHEME, PREC, STAGE>();
   const int ncw = (a.ncols + 32 * COLS - 1) / (32 * COLS);  // consumer warps; then producer, reducer
   const int64_t nz = a.nz;
   const int nv = a.nv;
-  const SlotLayout L = slot_layout<PREC>(nv, STAGE);
+  const int R = a.rows_per_slot;
+  const SlotLayout L = slot_layout<PREC>(nv, STAGE, R);
   const int D = a.ring;
 
   const int64_t z_begin = (int64_t)blockIdx.x * a.rows_per_cta;
@@ -333,42 +347,55 @@ __global__ void __launch_bounds__(stage_max_threads<SCHEME, PREC>())
     const Delta* din = static_cast<const Delta*>(a.d_in);
     const Delta* d1 = static_cast<const Delta*>(a.d1);
     const Delta* d2 = static_cast<const Delta*>(a.d2);
+    const int64_t nslots = (nrows + R - 1) / R;
+    const int64_t plane = nz * nv;
     int64_t issued = 0;
     int slot = 0;
     uint32_t fill = 0;  // how many times this slot has been filled before
-    for (int64_t j = 0; j < nrows; ++j) {
+    for (int64_t j = 0; j < nslots; ++j) {
       if (fill > 0 && !mbar_wait_or_abort(empty_bar(slot), (fill - 1) & 1u, abort_flag, a.err))
         break;
       fence_proxy_async();
       const uint32_t bar = full_bar(slot);
       const uint32_t base = smem_addr(ring + (size_t)slot * a.slot_bytes);
-      const int64_t i = i_first + j;
-      const int64_t r = wrap_row(i, nz);
-      const int64_t c = i - LAG;
-      const bool has_center = (STAGE == 4) && c >= z_begin && c < z_end;
-      const bool has_my = (PREC == kMIXED) && i >= z_begin && i < z_end;
-      uint32_t tx = 8 * rw + (STAGE > 1 ? 8 * rd : 0);
-      if (has_center) tx += 8 * ry + (PREC == kMIXED ? 24 : 16) * rd;
-      if (has_my) tx += 64;
+      const int64_t i0 = i_first + j * R;  // first leading row of the slot
+      const int nr = (int)min((int64_t)R, nrows - j * R);
+      const bool contiguous = i0 >= 0 && i0 + nr <= nz;  // no periodic wrap inside
+      // center rows c = i - lag of this slot that lie in the CTA's range (stage 4)
+      const int64_t c0 = i0 - LAG;
+      const int64_t cl = max(c0, z_begin), ch = min(c0 + nr, z_end);
+      const int ncen = (STAGE == 4 && ch > cl) ? (int)(ch - cl) : 0;
+      // leading rows in the CTA's range (running moments of y, mixed)
+      const int64_t il = max(i0, z_begin), ih = min(i0 + nr, z_end);
+      const int nmy = (PREC == kMIXED && ih > il) ? (int)(ih - il) : 0;
+      uint32_t tx = nr * (8 * rw + (STAGE > 1 ? 8 * rd : 0));
+      tx += ncen * ((PREC == kFP64 ? 8 * ry : 0) + 16 * rd);
+      tx += nmy * 64;
       mbar_arrive_expect_tx(bar, tx);
-      const int64_t plane = nz * nv;
-      const WinY* ysrc = ywin + r * nv;
 #pragma unroll 1
       for (int q = 0; q < 8; ++q) {
-        bulk_g2s(base + L.y_off + q * rw, ysrc + q * plane, rw, bar);
-        if (STAGE > 1) bulk_g2s(base + L.din_off + q * rd, din + r * nv + q * plane, rd, bar);
-      }
-      if (has_center) {
-#pragma unroll 1
-        for (int q = 0; q < 8; ++q) {
-          const int64_t o = q * plane + c * nv;
-          bulk_g2s(base + L.yc_off + q * ry, a.y_in + o, ry, bar);
-          bulk_g2s(base + L.d1c_off + q * rd, d1 + o, rd, bar);
-          bulk_g2s(base + L.d2c_off + q * rd, d2 + o, rd, bar);
-          if (PREC == kMIXED) bulk_g2s(base + L.d3c_off + q * rd, din + o, rd, bar);
+        const uint32_t dw = base + L.y_off + q * R * rw;
+        const uint32_t dd = base + L.din_off + q * R * rd;
+        if (contiguous) {
+          bulk_g2s(dw, ywin + q * plane + i0 * nv, nr * rw, bar);
+          if (STAGE > 1) bulk_g2s(dd, din + q * plane + i0 * nv, nr * rd, bar);
+        } else {
+          for (int r = 0; r < nr; ++r) {
+            const int64_t row = wrap_row(i0 + r, nz);
+            bulk_g2s(dw + r * rw, ywin + q * plane + row * nv, rw, bar);
+            if (STAGE > 1) bulk_g2s(dd + r * rd, din + q * plane + row * nv, rd, bar);
+          }
+        }
+        if (ncen > 0) {
+          const int off = (int)(cl - c0);
+          const int64_t o = q * plane + cl * nv;
+          if (PREC == kFP64)
+            bulk_g2s(base + L.yc_off + (q * R + off) * ry, a.y_in + o, ncen * ry, bar);
+          bulk_g2s(base + L.d1c_off + (q * R + off) * rd, d1 + o, ncen * rd, bar);
+          bulk_g2s(base + L.d2c_off + (q * R + off) * rd, d2 + o, ncen * rd, bar);
         }
       }
-      if (has_my) bulk_g2s(base + L.my_off, a.my + i * 8, 64, bar);
+      if (nmy > 0) bulk_g2s(base + L.my_off + (int)(il - i0) * 64, a.my + il * 8, nmy * 64, bar);
       issued = j + 1;
       if (++slot == D) {
         slot = 0;
@@ -383,33 +410,39 @@ __global__ void __launch_bounds__(stage_max_threads<SCHEME, PREC>())
 
   // =================================================================== reducer
   if (warp == ncw + 1) {
-    auto finish_dy = [&](int64_t rc) {  // mixed stage 4: advance the running moments of y
+    // mixed stage 4: advance the running moments of y by the increment's moments
+    auto finish_dy = [&](int64_t rc, double my_row) {
       const int m = (int)(rc % MS);
       if (!warp_wait(dy_bar(m), (uint32_t)((rc / MS) & 1))) return false;
       if (lane < 6) {
         Acc acc = Acc(0);
-        for (int w = 0; w < ncw; ++w) acc += partdy[(m * kMaxWarps + w) * 8 + lane];
-        a.my[(z_begin + rc) * 8 + lane] = myring[m * 8 + lane] + double(acc);
+        for (int w = 0; w < ncw; ++w) acc += partdy[(m * NW + w) * 8 + lane];
+        a.my[(z_begin + rc) * 8 + lane] = my_row + double(acc);
       }
       return true;
     };
+    double my_prev = 0.0;  // running y-moment (lane k) of the previous row
     for (int64_t rc = 0; rc < ncent; ++rc) {
       const int m = (int)(rc % MS);
       if (!warp_wait(part_bar(m), (uint32_t)((rc / MS) & 1))) return;
+      double my_cur = 0.0;
       if (lane < 6) {
         Acc acc = Acc(0);
         if (PREC == kFP64 || STAGE > 1)
-          for (int w = 0; w < ncw; ++w) acc += part[(m * kMaxWarps + w) * 8 + lane];
-        if (PREC == kMIXED)
-          momf[m * 8 + lane] = Acc(myring[m * 8 + lane] + double(acc));
-        else
+          for (int w = 0; w < ncw; ++w) acc += part[(m * NW + w) * 8 + lane];
+        if (PREC == kMIXED) {
+          my_cur = myring[m * 8 + lane];
+          momf[m * 8 + lane] = Acc(my_cur + double(acc));
+        } else {
           momf[m * 8 + lane] = acc;
+        }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(mom_bar(m));
-      if (PREC == kMIXED && STAGE == 4 && rc > 0 && !finish_dy(rc - 1)) return;
+      if (PREC == kMIXED && STAGE == 4 && rc > 0 && !finish_dy(rc - 1, my_prev)) return;
+      my_prev = my_cur;
     }
-    if (PREC == kMIXED && STAGE == 4 && ncent > 0) finish_dy(ncent - 1);
+    if (PREC == kMIXED && STAGE == 4 && ncent > 0) finish_dy(ncent - 1, my_prev);
     return;
   }
 
@@ -447,7 +480,7 @@ __global__ void __launch_bounds__(stage_max_threads<SCHEME, PREC>())
   const Real inv_dz = Real(a.inv_dz);
   const Real dt = Real(a.dt);
   const int64_t plane = nz * nv;
-  const int ecol = s * 4 * nv + vj0;  // element of component 0 in a slot row
+  const int rstride = R * nv;  // slot elements between component planes
 
   // Sliding window of this thread's columns: u[k] holds one row.
   Real u[WIN][4][COLS];
@@ -462,13 +495,21 @@ __global__ void __launch_bounds__(stage_max_threads<SCHEME, PREC>())
   for (int q = 0; q < 4; ++q)
 #pragma unroll
     for (int cc = 0; cc < COLS; ++cc) fprev[q][cc] = Real(0);
+  // mixed stage 4: raw delta_3 of the last lag+1 rows (the window holds y + delta_3)
+  Real dring[LAG + 1][4][COLS];
+#pragma unroll
+  for (int k = 0; k <= LAG; ++k)
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int cc = 0; cc < COLS; ++cc) dring[k][q][cc] = Real(0);
   bool nonfinite = false;
   bool stop = false;
   int slot = 0;
+  int rin = 0;       // row within the current slot
   uint32_t par = 0;  // phase parity of the current slot
   Delta* dout = static_cast<Delta*>(a.d_out) + (int64_t)(s * 4) * plane + vj0;
   double* yout = a.y_out + (int64_t)(s * 4) * plane + vj0;
-  float* y32out = a.y32_out + (int64_t)(s * 4) * plane + vj0;
 
   constexpr bool RING = Scheme<SCHEME>::kRing;
   auto row = [&](auto kc, int64_t j) {
@@ -495,8 +536,9 @@ __global__ void __launch_bounds__(stage_max_threads<SCHEME, PREC>())
     const bool lead_in_range = rl >= 0 && i < z_end;
     const bool center_in_range = rc >= 0 && c < z_end;
     const unsigned char* sb = ring + (size_t)slot * a.slot_bytes;
+    const int ecol = (s * 4 * R + rin) * nv + vj0;  // component 0 of this row in the slot
 
-    if (!warp_wait(full_bar(slot), par)) {
+    if (rin == 0 && !warp_wait(full_bar(slot), par)) {
       stop = true;
       return;
     }
@@ -504,14 +546,14 @@ __global__ void __launch_bounds__(stage_max_threads<SCHEME, PREC>())
     // ---- read the slot: leading row i (window arrays), center row c (stage 4)
     Real draw[4][COLS];
     double yc[4][COLS];
-    Real e1[4][COLS], e2[4][COLS], e3[4][COLS];
+    Real e1[4][COLS], e2[4][COLS];
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
       for (int cc = 0; cc < COLS; ++cc) {
         draw[q][cc] = Real(0);
         yc[q][cc] = 0.0;
-        e1[q][cc] = e2[q][cc] = e3[q][cc] = Real(0);
+        e1[q][cc] = e2[q][cc] = Real(0);
       }
     {
       using WinY = typename Prec<PREC>::WinY;
@@ -519,7 +561,7 @@ __global__ void __launch_bounds__(stage_max_threads<SCHEME, PREC>())
       const Delta* ds = reinterpret_cast<const Delta*>(sb + L.din_off);
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
-        const int e = ecol + q * nv;
+        const int e = ecol + q * rstride;
         WinY yv[COLS];
         Delta dd[COLS];
 #pragma unroll
@@ -541,31 +583,44 @@ __global__ void __launch_bounds__(stage_max_threads<SCHEME, PREC>())
         const double* ycs = reinterpret_cast<const double*>(sb + L.yc_off);
         const Delta* d1s = reinterpret_cast<const Delta*>(sb + L.d1c_off);
         const Delta* d2s = reinterpret_cast<const Delta*>(sb + L.d2c_off);
-        const Delta* d3s = reinterpret_cast<const Delta*>(sb + L.d3c_off);
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          const int e = ecol + q * nv;
-          Delta t1[COLS], t2[COLS], t3[COLS];
-          vload(ycs + e, yc[q]);
+          const int e = ecol + q * rstride;
+          Delta t1[COLS], t2[COLS];
+          if (PREC == kFP64) vload(ycs + e, yc[q]);
           vload(d1s + e, t1);
           vload(d2s + e, t2);
-          if (PREC == kMIXED) vload(d3s + e, t3);
 #pragma unroll
           for (int cc = 0; cc < COLS; ++cc) {
             e1[q][cc] = Real(t1[cc]);
             e2[q][cc] = Real(t2[cc]);
-            if (PREC == kMIXED) e3[q][cc] = Real(t3[cc]);
           }
         }
       }
       if (PREC == kMIXED && warp == 0 && lane < 6 && lead_in_range)
-        myring[(rl & (MS - 1)) * 8 + lane] = reinterpret_cast<const double*>(sb + L.my_off)[lane];
+        myring[(rl & (MS - 1)) * 8 + lane] =
+            reinterpret_cast<const double*>(sb + L.my_off + rin * 64)[lane];
     }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(empty_bar(slot));
-    if (++slot == D) {
-      slot = 0;
-      par ^= 1u;
+    if (PREC == kMIXED && STAGE == 4) {
+#pragma unroll
+      for (int k = 0; k < LAG; ++k)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int cc = 0; cc < COLS; ++cc) dring[k][q][cc] = dring[k + 1][q][cc];
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int cc = 0; cc < COLS; ++cc) dring[LAG][q][cc] = draw[q][cc];
+    }
+    if (++rin == R) {  // the whole slot has been read: hand it back to the producer
+      __syncwarp();
+      if (lane == 0) mbar_arrive(empty_bar(slot));
+      rin = 0;
+      if (++slot == D) {
+        slot = 0;
+        par ^= 1u;
+      }
     }
 
     // ---- partial velocity moments of row i (finished by the reducer)
@@ -590,7 +645,7 @@ __global__ void __launch_bounds__(stage_max_threads<SCHEME, PREC>())
         }
         const Real tot = warp_sum6_transposed(m6);
         const int k = (lane >> 2) & 7;
-        if ((lane & 3) == 0 && k < 6) part[(m * kMaxWarps + warp) * 8 + k] = tot;
+        if ((lane & 3) == 0 && k < 6) part[(m * NW + warp) * 8 + k] = tot;
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(part_bar(m));
@@ -671,32 +726,42 @@ __global__ void __launch_bounds__(stage_max_threads<SCHEME, PREC>())
         }
       } else {
         Real incr[4][COLS];
-        bool bad = false;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          double yn[COLS];
-          float y32n[COLS];
+        for (int q = 0; q < 4; ++q)
 #pragma unroll
           for (int cc = 0; cc < COLS; ++cc) {
             Real d3;
             if (PREC == kFP64)
               d3 = Real(double(u[CC][q][cc]) - yc[q][cc]);  // u = y + delta_3 at the center
             else
-              d3 = e3[q][cc];
+              d3 = dring[0][q][cc];
             incr[q][cc] = (e1[q][cc] + Real(2) * e2[q][cc] + d3) * Real(1.0 / 3.0) +
                           (dt * Real(1.0 / 6.0)) * kk[q][cc];
-            yn[cc] = yc[q][cc] +
-                     (PREC == kFP64 ? double(incr[q][cc]) : f2d_int(float(incr[q][cc])));
-            bad |= !is_finite_bits(yn[cc]);
-            if (PREC == kMIXED) y32n[cc] = d2f_rn_int(yn[cc]);
           }
+        if (PREC == kFP64) {
+          bool bad = false;
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            double yn[COLS];
+#pragma unroll
+            for (int cc = 0; cc < COLS; ++cc) {
+              yn[cc] = yc[q][cc] + double(incr[q][cc]);
+              bad |= !is_finite_bits(yn[cc]);
+            }
+            if (active) vstore(yout + rowoff + (int64_t)q * plane, yn);
+          }
+          nonfinite |= bad;
+        } else {
+          // the float increment; apply_increment_kernel adds it to y in double
           if (active) {
-            vstore(yout + rowoff + (int64_t)q * plane, yn);
-            if (PREC == kMIXED) vstore(y32out + rowoff + (int64_t)q * plane, y32n);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              Delta o[COLS];
+#pragma unroll
+              for (int cc = 0; cc < COLS; ++cc) o[cc] = Delta(incr[q][cc]);
+              vstore(dout + rowoff + (int64_t)q * plane, o);
+            }
           }
-        }
-        nonfinite |= bad;
-        if (PREC == kMIXED) {
           // float moments of the increment advance the FP64 running moments of y
           Real m6[6] = {Real(0), Real(0), Real(0), Real(0), Real(0), Real(0)};
 #pragma unroll
@@ -711,7 +776,7 @@ __global__ void __launch_bounds__(stage_max_threads<SCHEME, PREC>())
           }
           const Real tot = warp_sum6_transposed(m6);
           const int k = (lane >> 2) & 7;
-          if ((lane & 3) == 0 && k < 6) partdy[(m * kMaxWarps + warp) * 8 + k] = tot;
+          if ((lane & 3) == 0 && k < 6) partdy[(m * NW + warp) * 8 + k] = tot;
           __syncwarp();
           if (lane == 0) mbar_arrive(dy_bar(m));
         }
@@ -738,7 +803,7 @@ __global__ void __launch_bounds__(stage_max_threads<SCHEME, PREC>())
     for (int64_t j = 0; j < nrows && !stop; ++j) row(std::integral_constant<int, 0>{}, j);
   }
 
-  if (STAGE == 4) {
+  if (STAGE == 4 && PREC == kFP64) {
     const unsigned any = __ballot_sync(0xffffffffu, nonfinite);
     if (lane == 0 && any) atomicOr(a.err, kErrNonFinite);
   }
