@@ -20,9 +20,9 @@ constexpr uint32_t kErrTimeout = 2u;
 // A bounded wait gives up after this many SM clock cycles (about 2 s).
 constexpr long long kWaitLimitCycles = 4000000000LL;
 
-// Ring of moment slots per CTA.  Consumer warps drift apart by at most the
-// bulk-copy ring depth (kMaxRing rows), so a slot is reused only after
-// kMomSlots > lag + kMaxRing rows.
+// Ring of moment slots per CTA.  Consumer warps drift apart by at most
+// (ring depth) x (rows per slot) rows; the launch configuration keeps that at
+// most kMomSlots - 2 so that the per-row barriers of the ring stay unambiguous.
 constexpr int kMomSlots = 16;
 constexpr int kMaxRing = 8;
 constexpr int kMaxWarps = 16;  // consumer warps: 2 * nv / 32 with nv <= 256
