@@ -127,7 +127,7 @@ class ClockSampler:
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("stage_kernel.cuh", "cosenu_device.cuh"):
+    for f in ("stage_kernel.cuh", "stage_body.inc", "cosenu_device.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2203_12866_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -279,6 +279,82 @@ def run_variant(b, scheme, prec, steps, warmup, device, stream, state_dev):
         b.cosenu_destroy(h)
 
 
+BATCH_WORKLOAD = ("batched run: 256 independent grids, nz log-uniform [1024, 32768], "
+                  "nv in {32, 64, 128}, mu log-uniform [0.1, 10], alpha U[0.7, 1.2], "
+                  "sigma_nu, sigma_nubar U[0.3, 0.8], scheme FD+KO or WENO7 at random, "
+                  "dz = 0.2/mu, dt = 0.4 dz, mixed precision, seed 12866")
+
+
+def run_batched(args, device, hbm_peak):
+    """The batched solver on the 256-grid workload: tuned launch shapes, then
+    args.batch_steps steps timed with CUDA events on the batch's stream."""
+    import torch
+
+    from paper_2203_12866_gb300 import binding as b
+    from paper_2203_12866_gb300 import inputs
+
+    specs = inputs.batch_instances(args.batch_n)
+    bt = b.Batch()
+    try:
+        cells = reals = 0
+        for sp in specs:
+            m = bt.add(sp["nz"], sp["nv"], sp["L"], sp["scheme"], b.COSENU_MIXED, mu=sp["mu"],
+                       dt=sp["dt"])
+            st = inputs.collective_state_device(sp["nz"], sp["nv"], device, alpha=sp["alpha"],
+                                                sigma_nu=sp["sigma_nu"],
+                                                sigma_nubar=sp["sigma_nubar"], seed=sp["seed"])
+            torch.cuda.synchronize(device)
+            b.cosenu_set_state_device(m.h, st.data_ptr(), st.numel())
+            torch.cuda.synchronize(device)
+            del st
+            cells += 2 * sp["nz"] * sp["nv"]
+            reals += 8 * sp["nz"] * sp["nv"]
+        t0 = time.perf_counter()
+        tuned = bt.tune(reps=1)
+        tune_s = time.perf_counter() - t0
+        bt.step(args.warmup)
+        rc, bad = bt.sync()
+        stream = torch.cuda.ExternalStream(b.cosenu_batch_stream(bt.b), device=device)
+        l0 = b.cosenu_kernel_launches()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        bt.step(args.batch_steps)
+        e1.record(stream)
+        e1.synchronize()
+        launches = b.cosenu_kernel_launches() - l0
+        ms = e0.elapsed_time(e1) / args.batch_steps
+        # per-kernel device times of a few directly launched steps (classes in series)
+        b.cosenu_batch_set_stage_timing(bt.b, True)
+        b.cosenu_batch_stage_times(bt.b)
+        bt.step(2)
+        kms, kn = b.cosenu_batch_stage_times(bt.b)
+        b.cosenu_batch_set_stage_timing(bt.b, False)
+        rc2, bad2 = bt.sync()
+        alg = sum(STAGE_BYTES["mixed"]) * reals
+        classes = bt.classes()
+        for c in classes:  # achieved bandwidth of each class's kernels
+            creals = 8 * c["rows"] * c["nv"]
+            c["kernel_GBs"] = [STAGE_BYTES["mixed"][k] * creals / (ms_k * 1e-3) / 1e9
+                               if ms_k > 0 else None for k, ms_k in enumerate(c["kernel_ms"])]
+            c["class_ms_per_step"] = sum(c["kernel_ms"])
+        return {
+            "workload": BATCH_WORKLOAD, "grids": len(specs), "cells_per_step": cells,
+            "value": cells / (ms * 1e-3), "unit": "cell-updates/s", "ms_per_step": ms,
+            "steps": args.batch_steps, "warmup": args.warmup, "tune_steps": tuned,
+            "tune_s": tune_s, "gpu_launches": launches,
+            "hbm": {"achieved": alg / (ms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                    "frac": alg / (ms * 1e-3) / 1e9 / hbm_peak,
+                    "alg_bytes_per_step": alg, "bytes_per_real": sum(STAGE_BYTES["mixed"])},
+            "kernel_ms_per_step": {KERNEL_NAMES[k]: float(kms[k] / 2) for k in range(5)},
+            "classes": classes, "device_bytes": bt.device_bytes(),
+            "flags": [rc, bad, rc2, bad2],
+        }
+    finally:
+        bt.close()
+        torch.cuda.empty_cache()
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -387,6 +463,8 @@ def run_ours(args, world, rank, local):
     del state
     torch.cuda.empty_cache()
 
+    batched = run_batched(args, device, hbm_peak) if args.batched else None
+
     # ---- oracle on the host cores (rank 0, one GPU only)
     cpu = None
     if args.cpu_baseline and world == 1 and rank == 0:
@@ -408,7 +486,7 @@ def run_ours(args, world, rank, local):
                        "l2": "inputs larger than L2 (state 17.2 GB >> 129 MB)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clk, "variants": variants,
+            "clocks": clk, "variants": variants, "batched": batched,
             "conserved_after": {"tr_nu": cons["tr_nu"], "M": list(cons["M"]),
                                 "dP_max": cons["dP_max"]},
         }
@@ -429,6 +507,9 @@ def main():
     ap.add_argument("--cpu-rows", type=int, default=65536)
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-batched", dest="batched", action="store_false")
+    ap.add_argument("--batch-n", type=int, default=256)
+    ap.add_argument("--batch-steps", type=int, default=20)
     ap.add_argument("--nz", type=int, default=NZ_FULL,
                     help="z cells (smaller values only for profiling captures)")
     args = ap.parse_args()

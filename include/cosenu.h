@@ -184,6 +184,106 @@ const char* cosenu_last_error(cosenu_t h);
 /* Kernel launches the library has issued in this process (all handles). */
 uint64_t cosenu_kernel_launches(void);
 
+/* ------------------------------------------------------------------------
+ * Batched solver: many independent grids advanced together.
+ *
+ * Every cell of every member is computed with exactly the arithmetic of a
+ * single handle (the same kernels, the same summation order), so a member's
+ * state after n batched steps is bit-identical to the same handle stepped n
+ * times alone.  Members are grouped into classes of equal (scheme, precision,
+ * nv); each class runs one fused kernel per RK4 stage over all of its members'
+ * z rows (work items of whole or partial grids per CTA), plus, for the mixed
+ * precision, one state-increment kernel per class.  Classes are independent
+ * chains of kernels, replayed from one CUDA graph as parallel branches.
+ *
+ * Member handles are created by the batch and share its stream.  Use the
+ * single-handle calls on them for everything except stepping and stream
+ * control: cosenu_set_params, cosenu_set_state(_device), cosenu_get_state,
+ * cosenu_get_rows, cosenu_moments, cosenu_conserved (all ordered with the
+ * batch's steps).  cosenu_step on a member steps that member alone.
+ * cosenu_set_stream on a member fails with COSENU_EINVAL; cosenu_destroy
+ * ignores a member (remove it with cosenu_batch_remove).  A batch is not
+ * thread-safe.
+ */
+typedef struct cosenu_batch_s* cosenu_batch_t;
+
+/* An empty batch on the current device, with its own stream.  NULL on
+ * failure (reason in cosenu_last_error(NULL)). */
+cosenu_batch_t cosenu_batch_create(void);
+
+/* Destroy the batch and all of its members.  NULL is a no-op. */
+void cosenu_batch_destroy(cosenu_batch_t b);
+
+/* Add a member grid (arguments as cosenu_create); *member receives its handle.
+ * The state starts at zero and the parameters at their defaults. */
+int cosenu_batch_add(cosenu_batch_t b, int64_t nz, int32_t nv, double L, int scheme,
+                     int precision, cosenu_t* member);
+
+/* Remove a member and release its device memory (waits for the stream). */
+int cosenu_batch_remove(cosenu_batch_t b, cosenu_t member);
+
+/* Number of members. */
+int32_t cosenu_batch_size(cosenu_batch_t b);
+
+/* Device bytes held by the members' workspaces plus the batch's launch tables. */
+size_t cosenu_batch_device_bytes(cosenu_batch_t b);
+
+/* Enqueue nsteps RK4 steps of every member on the batch's stream and return.
+ * The launch plan (classes, work items, graph) is rebuilt here when members or
+ * their parameters changed since the last call. */
+int cosenu_batch_step(cosenu_batch_t b, int64_t nsteps);
+
+/* Wait for the batch's stream and check every member's error flags (then
+ * clear them).  Returns COSENU_ENONFINITE / COSENU_ETIMEOUT like cosenu_sync;
+ * *first_bad (may be NULL) receives the index (in cosenu_batch_member order)
+ * of the first member with a flag, or -1. */
+int cosenu_batch_sync(cosenu_batch_t b, int32_t* first_bad);
+
+/* Handle of member i (0 <= i < cosenu_batch_size), in the order of addition
+ * (removal closes the gap).  NULL if out of range. */
+cosenu_t cosenu_batch_member(cosenu_batch_t b, int32_t i);
+
+/* Empirical autotuner.  For every (class, stage) it times the candidate launch
+ * shapes -- the ring shapes (rows per bulk copy, ring depth) with the best
+ * copy sizes, and work items sized for 1, 2 or 4 times the resident CTAs --
+ * on real steps of the batch (reps steps per candidate; the members advance by
+ * these steps, with results that do not depend on the shape), keeps the
+ * fastest, then times whole steps with the classes in series and as parallel
+ * graph branches and keeps the faster.  *steps_taken (may be NULL) receives
+ * the number of steps the members advanced.  The choice is kept per class key
+ * (scheme, precision, nv) across later membership changes. */
+int cosenu_batch_tune(cosenu_batch_t b, int32_t reps, int64_t* steps_taken);
+
+/* Launch plan of class c (0 <= c < cosenu_batch_classes()), after the last
+ * step or tune call.  Per stage s (index s - 1 for stages 1..4): rows per
+ * bulk copy, ring slots, CTAs (work items), shared memory bytes and resident
+ * CTAs per SM.  kernel_ms[k - 1]: mean device time of one launch of kernel k
+ * (1..4 stages, 5 increment) in the steps timed before the last
+ * cosenu_batch_stage_times call (0 if none). */
+typedef struct {
+  int32_t scheme, precision, nv, members;
+  int64_t rows;  /* sum of the members' nz */
+  int32_t rows_per_slot[4], ring[4], grid[4], smem[4], occupancy[4];
+  int32_t concurrent; /* 1: classes run as parallel graph branches */
+  double kernel_ms[5];
+} cosenu_batch_class;
+int32_t cosenu_batch_classes(cosenu_batch_t b);
+int cosenu_batch_class_info(cosenu_batch_t b, int32_t c, cosenu_batch_class* out);
+
+/* Kernel timing of batched steps, summed over classes, as cosenu_stage_times
+ * (k = 1..4 the stage kernels, k = 5 the increment kernels).  Timed steps are
+ * launched directly with the classes in series, so that each kernel's time is
+ * its own. */
+int cosenu_batch_set_stage_timing(cosenu_batch_t b, int on);
+int cosenu_batch_stage_times(cosenu_batch_t b, double* ms, int64_t* n);
+
+/* The batch's cudaStream_t (for events or for ordering other work with its
+ * steps); owned by the batch. */
+void* cosenu_batch_stream(cosenu_batch_t b);
+
+/* Description of the last error of b (of this thread for b = NULL). */
+const char* cosenu_batch_last_error(cosenu_batch_t b);
+
 /* Conserved-quantity diagnostics without any device allocation.  (The paper has
  * no counterpart: this entry point exists for callers of this library.)
  *

@@ -28,7 +28,13 @@ EXPORTS = (
     "cosenu_step",
     "cosenu_sync", "cosenu_moments", "cosenu_conserved", "cosenu_set_stage_timing",
     "cosenu_stage_times", "cosenu_steps_taken",
-    "cosenu_last_error", "cosenu_kernel_launches", "cosenu_conserved_noalloc",
+    "cosenu_last_error", "cosenu_kernel_launches",
+    "cosenu_batch_create", "cosenu_batch_destroy", "cosenu_batch_add", "cosenu_batch_remove",
+    "cosenu_batch_size", "cosenu_batch_device_bytes", "cosenu_batch_step", "cosenu_batch_sync",
+    "cosenu_batch_member", "cosenu_batch_tune", "cosenu_batch_classes",
+    "cosenu_batch_class_info", "cosenu_batch_set_stage_timing", "cosenu_batch_stage_times",
+    "cosenu_batch_stream", "cosenu_batch_last_error",
+    "cosenu_conserved_noalloc",
 )
 
 
@@ -42,6 +48,15 @@ class cosenu_conserved_t(ctypes.Structure):
                 ("M", ctypes.c_double * 3), ("M_vac", ctypes.c_double),
                 ("dP_max", ctypes.c_double), ("dP_mean", ctypes.c_double),
                 ("step", ctypes.c_int64)]
+
+
+class cosenu_batch_class(ctypes.Structure):
+    _fields_ = [("scheme", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("nv", ctypes.c_int32), ("members", ctypes.c_int32), ("rows", ctypes.c_int64),
+                ("rows_per_slot", ctypes.c_int32 * 4), ("ring", ctypes.c_int32 * 4),
+                ("grid", ctypes.c_int32 * 4), ("smem", ctypes.c_int32 * 4),
+                ("occupancy", ctypes.c_int32 * 4), ("concurrent", ctypes.c_int32),
+                ("kernel_ms", ctypes.c_double * 5)]
 
 
 class CosenuError(RuntimeError):
@@ -88,6 +103,23 @@ def load(path: str = LIB_PATH):
         "cosenu_kernel_launches": (ctypes.c_uint64, []),
         "cosenu_conserved_noalloc": (ctypes.c_int, [vp, i64, i32, ctypes.c_double, ctypes.c_double,
                                                     vp, vp]),
+        "cosenu_batch_create": (vp, []),
+        "cosenu_batch_destroy": (None, [vp]),
+        "cosenu_batch_add": (ctypes.c_int, [vp, i64, i32, ctypes.c_double, ctypes.c_int,
+                                            ctypes.c_int, ctypes.POINTER(vp)]),
+        "cosenu_batch_remove": (ctypes.c_int, [vp, vp]),
+        "cosenu_batch_size": (i32, [vp]),
+        "cosenu_batch_device_bytes": (sz, [vp]),
+        "cosenu_batch_step": (ctypes.c_int, [vp, i64]),
+        "cosenu_batch_sync": (ctypes.c_int, [vp, ctypes.POINTER(i32)]),
+        "cosenu_batch_member": (vp, [vp, i32]),
+        "cosenu_batch_tune": (ctypes.c_int, [vp, i32, ctypes.POINTER(i64)]),
+        "cosenu_batch_classes": (i32, [vp]),
+        "cosenu_batch_class_info": (ctypes.c_int, [vp, i32, ctypes.POINTER(cosenu_batch_class)]),
+        "cosenu_batch_set_stage_timing": (ctypes.c_int, [vp, ctypes.c_int]),
+        "cosenu_batch_stage_times": (ctypes.c_int, [vp, dp, ctypes.POINTER(i64)]),
+        "cosenu_batch_stream": (vp, [vp]),
+        "cosenu_batch_last_error": (ctypes.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -227,7 +259,107 @@ def cosenu_conserved_noalloc(y_dev_ptr, nz, nv, L, theta, out_dev_ptr, stream_ha
     return _check(None, rc)
 
 
-# ---------------------------------------------------------------- owner object
+# ---------------------------------------------------------------- batched solver
+
+def _bcheck(b, rc):
+    if rc != COSENU_OK:
+        raise CosenuError(rc, load().cosenu_batch_last_error(b).decode())
+    return rc
+
+
+def cosenu_batch_create():
+    lib = load()
+    b = lib.cosenu_batch_create()
+    if not b:
+        raise CosenuError(COSENU_ECUDA, lib.cosenu_batch_last_error(None).decode())
+    return b
+
+
+def cosenu_batch_destroy(b):
+    load().cosenu_batch_destroy(b)
+
+
+def cosenu_batch_add(b, nz, nv, L, scheme=COSENU_FDKO, precision=COSENU_MIXED):
+    h = ctypes.c_void_p()
+    _bcheck(b, load().cosenu_batch_add(b, int(nz), int(nv), float(L), int(scheme), int(precision),
+                                       ctypes.byref(h)))
+    return h.value
+
+
+def cosenu_batch_remove(b, member):
+    return _bcheck(b, load().cosenu_batch_remove(b, member))
+
+
+def cosenu_batch_size(b):
+    return int(load().cosenu_batch_size(b))
+
+
+def cosenu_batch_device_bytes(b):
+    return int(load().cosenu_batch_device_bytes(b))
+
+
+def cosenu_batch_step(b, nsteps=1):
+    return _bcheck(b, load().cosenu_batch_step(b, int(nsteps)))
+
+
+def cosenu_batch_sync(b):
+    """Returns (rc, first_bad) without raising on COSENU_ENONFINITE / COSENU_ETIMEOUT."""
+    bad = ctypes.c_int32(-1)
+    rc = load().cosenu_batch_sync(b, ctypes.byref(bad))
+    if rc not in (COSENU_OK, COSENU_ENONFINITE, COSENU_ETIMEOUT):
+        _bcheck(b, rc)
+    return rc, int(bad.value)
+
+
+def cosenu_batch_member(b, i):
+    return load().cosenu_batch_member(b, int(i))
+
+
+def cosenu_batch_tune(b, reps=2):
+    """Run the autotuner; returns the number of steps the members advanced."""
+    n = ctypes.c_int64(0)
+    _bcheck(b, load().cosenu_batch_tune(b, int(reps), ctypes.byref(n)))
+    return int(n.value)
+
+
+def cosenu_batch_classes(b):
+    n = int(load().cosenu_batch_classes(b))
+    if n < 0:
+        raise CosenuError(COSENU_ECUDA, load().cosenu_batch_last_error(b).decode())
+    return n
+
+
+def cosenu_batch_class_info(b, c):
+    info = cosenu_batch_class()
+    _bcheck(b, load().cosenu_batch_class_info(b, int(c), ctypes.byref(info)))
+    return {"scheme": info.scheme, "precision": info.precision, "nv": info.nv,
+            "members": info.members, "rows": info.rows,
+            "rows_per_slot": list(info.rows_per_slot), "ring": list(info.ring),
+            "grid": list(info.grid), "smem": list(info.smem),
+            "occupancy": list(info.occupancy), "concurrent": bool(info.concurrent),
+            "kernel_ms": list(info.kernel_ms)}
+
+
+def cosenu_batch_set_stage_timing(b, on=True):
+    return _bcheck(b, load().cosenu_batch_set_stage_timing(b, 1 if on else 0))
+
+
+def cosenu_batch_stage_times(b):
+    ms = np.zeros(5)
+    n = (ctypes.c_int64 * 5)()
+    _bcheck(b, load().cosenu_batch_stage_times(b, _dptr(ms), n))
+    return ms, np.array(n[:], dtype=np.int64)
+
+
+def cosenu_batch_stream(b):
+    return int(load().cosenu_batch_stream(b) or 0)
+
+
+def cosenu_batch_last_error(b=None):
+    return load().cosenu_batch_last_error(b).decode()
+
+
+# ---------------------------------------------------------------- owner objects
 
 class Solver:
     """Owns one handle: Solver(nz, nv, L, scheme, precision, **params)."""
@@ -288,3 +420,70 @@ class Solver:
         p = cosenu_get_params(self.h)
         return {"mu": p.mu, "omega": p.omega, "theta": p.theta, "lambda": p.lambda_,
                 "ko_eps": p.ko_eps, "weno_eps": p.weno_eps, "dt": p.dt}
+
+
+class Member(Solver):
+    """A grid of a Batch: the Solver calls, without ownership of the handle."""
+
+    def __init__(self, batch, h, nz, nv, L):
+        self.batch = batch
+        self.nz, self.nv, self.L = int(nz), int(nv), float(L)
+        self.h = h
+
+    def close(self):
+        self.h = None  # the batch owns the handle
+
+
+class Batch:
+    """Owns one batched solver; add() returns Member objects."""
+
+    def __init__(self):
+        self.b = cosenu_batch_create()
+        self.members = []
+
+    def close(self):
+        if self.b:
+            for m in self.members:
+                m.h = None
+            cosenu_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def add(self, nz, nv, L, scheme=COSENU_FDKO, precision=COSENU_MIXED, **params):
+        h = cosenu_batch_add(self.b, nz, nv, L, scheme, precision)
+        m = Member(self, h, nz, nv, L)
+        if params:
+            cosenu_set_params(h, **params)
+        self.members.append(m)
+        return m
+
+    def remove(self, m):
+        cosenu_batch_remove(self.b, m.h)
+        self.members.remove(m)
+        m.h = None
+
+    def step(self, n=1):
+        cosenu_batch_step(self.b, n)
+
+    def sync(self):
+        return cosenu_batch_sync(self.b)
+
+    def tune(self, reps=2):
+        return cosenu_batch_tune(self.b, reps)
+
+    def classes(self):
+        return [cosenu_batch_class_info(self.b, c) for c in range(cosenu_batch_classes(self.b))]
+
+    def device_bytes(self):
+        return cosenu_batch_device_bytes(self.b)

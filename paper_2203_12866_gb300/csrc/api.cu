@@ -8,6 +8,7 @@
 // four fused stage kernels of each RK4 step (plus the increment kernel in the
 // mixed path) on the handle's stream; pairs of steps are replayed from a CUDA
 // graph when the stream allows capture.
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -17,7 +18,7 @@
 
 #include "../../include/cosenu.h"
 #include "diag_kernels.cuh"
-#include "stage_launch.cuh"
+#include "engine.cuh"
 
 using namespace cosenu;
 
@@ -28,19 +29,8 @@ thread_local std::string tl_error;
 
 constexpr size_t kAlign = 256;
 constexpr int64_t kMinRowsPerCta = 16;
-constexpr int kSmemLimit = 232448;
 
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
-
-struct StageCfg {
-  int grid = 0, block = 0, ring = 0, rows_per_slot = 1, slot_bytes = 0;
-  int64_t rows = 0;
-  size_t smem = 0;
-};
-
-struct Layout {
-  size_t y0, y1, y32a, y32b, d1, d2, d3, my, zavg, partial, result, err, total;
-};
 
 bool valid_sizes(int64_t nz, int32_t nv, int scheme, int precision) {
   return nz >= 1 && nv >= 4 && nv <= 256 && nv % 4 == 0 &&
@@ -79,33 +69,6 @@ void set_thread_error(const std::string& msg) { tl_error = msg; }
 void count_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
 }  // namespace cosenu
 
-struct cosenu_s {
-  int64_t nz = 0;
-  int32_t nv = 0;
-  double L = 0;
-  int scheme = 0, precision = 0;
-  cosenu_params p{};
-  cudaStream_t stream = nullptr;
-  bool own_stream = false;
-  bool own_mem = false;
-  unsigned char* ws = nullptr;
-  Layout lay{};
-  double* y[2] = {nullptr, nullptr};
-  float* y32[2] = {nullptr, nullptr};  // mixed: float copy of y[0]
-  int ycur = 0;
-  void* d[3] = {nullptr, nullptr, nullptr};
-  double* my = nullptr;
-  uint32_t* err = nullptr;
-  StageCfg cfg[5];
-  int nsm = 0;
-  cudaGraphExec_t graph = nullptr;  // two RK4 steps starting from y[0]
-  bool timing = false;
-  std::vector<cudaEvent_t> ev_free;                    // reusable events
-  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[6];  // per kernel: (start, stop)
-  int64_t steps = 0;
-  std::string error;
-};
-
 namespace {
 
 int fail(cosenu_t h, int code, const std::string& msg) {
@@ -126,51 +89,60 @@ int cuda_fail(cosenu_t h, cudaError_t e, const char* what) {
     if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
   } while (0)
 
-// Every pointer a stage kernel dereferences must be set (a launch with a
-// missing buffer is refused instead of faulting on the device).
-bool stage_args_complete(const cosenu_s* h, int stage, const StageArgs& a) {
-  const bool mixed = h->precision == COSENU_MIXED;
-  if (!a.err || (mixed ? !a.y32_in || !a.my : !a.y_in)) return false;
-  if (stage > 1 && !a.d_in) return false;
-  if ((stage < 4 || mixed) && !a.d_out) return false;
-  if (stage == 4 && (!a.d1 || !a.d2 || (!mixed && !a.y_out))) return false;
-  return true;
-}
-
 cudaError_t launch_stage(cosenu_t h, int stage, const StageArgs& a) {
   const StageCfg& c = h->cfg[stage];
-  if (!stage_args_complete(h, stage, a)) return cudaErrorInvalidValue;
-  cudaError_t e;
-  if (h->scheme == COSENU_FDKO && h->precision == COSENU_FP64)
-    e = launch_rk4_stage<kFDKO, kFP64>(stage, a, c.grid, c.block, c.smem, h->stream);
-  else if (h->scheme == COSENU_FDKO)
-    e = launch_rk4_stage<kFDKO, kMIXED>(stage, a, c.grid, c.block, c.smem, h->stream);
-  else if (h->precision == COSENU_FP64)
-    e = launch_rk4_stage<kWENO7, kFP64>(stage, a, c.grid, c.block, c.smem, h->stream);
-  else
-    e = launch_rk4_stage<kWENO7, kMIXED>(stage, a, c.grid, c.block, c.smem, h->stream);
+  cudaError_t e = launch_stage_kernel(h->scheme, h->precision, stage, a, nullptr, c.grid, c.block,
+                                      c.smem, h->stream);
   if (e == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
   return e;
 }
 
-int max_blocks(cosenu_t h, int stage, int block, size_t smem) {
-  if (h->scheme == COSENU_FDKO && h->precision == COSENU_FP64)
-    return stage_max_blocks_per_sm<kFDKO, kFP64>(stage, block, smem);
-  if (h->scheme == COSENU_FDKO) return stage_max_blocks_per_sm<kFDKO, kMIXED>(stage, block, smem);
-  if (h->precision == COSENU_FP64)
-    return stage_max_blocks_per_sm<kWENO7, kFP64>(stage, block, smem);
-  return stage_max_blocks_per_sm<kWENO7, kMIXED>(stage, block, smem);
+// Launch shape of each stage: the best ring shape of ring_choices() and a
+// persistent grid of at most SMs x resident CTAs, contiguous z ranges of at
+// least kMinRowsPerCta rows.
+int configure(cosenu_t h) {
+  int dev = 0, nsm = 0;
+  CK(h, cudaGetDevice(&dev));
+  CK(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+  h->nsm = nsm;
+  for (int s = 1; s <= 4; ++s) {
+    bool qfail = false;
+    const std::vector<RingChoice> rc =
+        ring_choices(h->scheme, h->precision, h->nv, s, false, &qfail);
+    if (qfail) return fail(h, COSENU_ECUDA, "occupancy query failed");
+    if (rc.empty()) return fail(h, COSENU_EINVAL, "grid row does not fit in shared memory");
+    const RingChoice& best = rc.front();
+    StageCfg c;
+    c.block = stage_block(h->scheme, h->precision, h->nv, s);
+    c.ring = best.ring;
+    c.rows_per_slot = best.rows_per_slot;
+    c.slot_bytes = best.slot_bytes;
+    c.smem = best.smem;
+    const int64_t max_grid = (int64_t)nsm * best.occ;
+    int64_t grid = (h->nz + kMinRowsPerCta - 1) / kMinRowsPerCta;
+    if (grid > max_grid) grid = max_grid;
+    if (grid < 1) grid = 1;
+    c.rows = (h->nz + grid - 1) / grid;
+    c.grid = (int)((h->nz + c.rows - 1) / c.rows);
+    h->cfg[s] = c;
+  }
+  return COSENU_OK;
 }
 
-// Per-stage launch traits of the (scheme, precision) pair of a handle.
+}  // namespace
+
+namespace cosenu {
+
+namespace {
+
+// Per-stage launch traits of a (scheme, precision) pair.
 struct StageTraits {
   int cols, header;
 };
 
 template <int SCHEME, int PREC, int STAGE>
 StageTraits traits_of() {
-  return {cosenu::stage_cols<SCHEME, PREC, STAGE>(),
-          cosenu::stage_smem_header_bytes<SCHEME, PREC, STAGE>()};
+  return {stage_cols<SCHEME, PREC, STAGE>(), stage_smem_header_bytes<SCHEME, PREC, STAGE>()};
 }
 
 template <int SCHEME, int PREC>
@@ -183,81 +155,104 @@ StageTraits traits_for_stage(int stage) {
   }
 }
 
-StageTraits stage_traits(cosenu_t h, int stage) {
-  if (h->scheme == COSENU_FDKO)
-    return h->precision == COSENU_FP64 ? traits_for_stage<kFDKO, kFP64>(stage)
-                                       : traits_for_stage<kFDKO, kMIXED>(stage);
-  return h->precision == COSENU_FP64 ? traits_for_stage<kWENO7, kFP64>(stage)
-                                     : traits_for_stage<kWENO7, kMIXED>(stage);
+StageTraits stage_traits(int scheme, int precision, int stage) {
+  if (scheme == COSENU_FDKO)
+    return precision == COSENU_FP64 ? traits_for_stage<kFDKO, kFP64>(stage)
+                                    : traits_for_stage<kFDKO, kMIXED>(stage);
+  return precision == COSENU_FP64 ? traits_for_stage<kWENO7, kFP64>(stage)
+                                  : traits_for_stage<kWENO7, kMIXED>(stage);
 }
 
-int slot_bytes(cosenu_t h, int stage, int rows) {
-  return h->precision == COSENU_FP64 ? slot_layout<kFP64>(h->nv, stage, rows).bytes
-                                     : slot_layout<kMIXED>(h->nv, stage, rows).bytes;
+int max_blocks(int scheme, int precision, int stage, bool batched, int block, size_t smem) {
+  if (scheme == COSENU_FDKO && precision == COSENU_FP64)
+    return stage_max_blocks_per_sm<kFDKO, kFP64>(stage, batched, block, smem);
+  if (scheme == COSENU_FDKO)
+    return stage_max_blocks_per_sm<kFDKO, kMIXED>(stage, batched, block, smem);
+  if (precision == COSENU_FP64)
+    return stage_max_blocks_per_sm<kWENO7, kFP64>(stage, batched, block, smem);
+  return stage_max_blocks_per_sm<kWENO7, kMIXED>(stage, batched, block, smem);
 }
 
-// Launch shape of each stage.  One thread per (species, v) column pair (FD4+KO)
-// or column (WENO7), plus a producer and a reducer warp.  The ring: R z rows
-// per slot (one bulk copy per component plane moves R rows) and D >= 2 slots;
-// among the (R, D) that fit, take the largest copy size times resident CTAs
-// (up to 4 KB), then the most resident CTAs, then the deepest ring.  Persistent
-// grid: at most SMs x resident CTAs, contiguous z ranges of at least
-// kMinRowsPerCta rows.
-int configure(cosenu_t h) {
-  int dev = 0, nsm = 0;
-  CK(h, cudaGetDevice(&dev));
-  CK(h, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-  h->nsm = nsm;
-  for (int s = 1; s <= 4; ++s) {
-    const StageTraits tr = stage_traits(h, s);
-    StageCfg c;
-    c.block = ((2 * h->nv + 32 * tr.cols - 1) / (32 * tr.cols)) * 32 + 64;
-    int64_t best_score = -1;
-    int best_occ = 0, best_d = 0, best_r = 0;
-    for (int R = 1; R <= 32; R *= 2) {
-      const int slot = slot_bytes(h, s, R);
-      for (int D = 2; D <= kMaxRing; ++D) {
-        // Consumer warps drift apart by at most D * R rows; the moment-slot
-        // barriers stay unambiguous only while that is <= kMomSlots - 2.
-        if (D * R > kMomSlots - 2) break;
-        const size_t smem = (size_t)tr.header + (size_t)D * slot;
-        if (smem > (size_t)kSmemLimit) break;
-        const int occ = max_blocks(h, s, c.block, smem);
-        if (occ < 0) return fail(h, COSENU_ECUDA, "occupancy query failed");
-        if (occ <= 0) continue;
-        // Bandwidth depends mostly on the contiguous bytes each bulk copy moves
-        // per component plane (R rows of nv floats) times the resident CTAs:
-        // ~1 KB per copy reaches about 40% of HBM peak, 2 KB with two CTAs or
-        // 4 KB with one about 95% (measured on GB300).
-        const int64_t score = std::min<int64_t>((int64_t)R * h->nv * 4 * occ, 4096);
-        const bool better = score > best_score ||
-                            (score == best_score &&
-                             (occ > best_occ || (occ == best_occ && D > best_d)));
-        if (better) {
-          best_score = score;
-          best_occ = occ;
-          best_d = D;
-          best_r = R;
-        }
+int slot_bytes_of(int precision, int nv, int stage, int rows) {
+  return precision == COSENU_FP64 ? slot_layout<kFP64>(nv, stage, rows).bytes
+                                  : slot_layout<kMIXED>(nv, stage, rows).bytes;
+}
+
+}  // namespace
+
+// Every pointer a stage kernel dereferences must be set (a launch with a
+// missing buffer is refused instead of faulting on the device).
+bool stage_args_complete(int precision, int stage, const StageArgs& a) {
+  const bool mixed = precision == COSENU_MIXED;
+  if (!a.err || (mixed ? !a.y32_in || !a.my : !a.y_in)) return false;
+  if (stage > 1 && !a.d_in) return false;
+  if ((stage < 4 || mixed) && !a.d_out) return false;
+  if (stage == 4 && (!a.d1 || !a.d2 || (!mixed && !a.y_out))) return false;
+  return true;
+}
+
+int stage_block(int scheme, int precision, int nv, int stage) {
+  const int cols = stage_traits(scheme, precision, stage).cols;
+  return ((2 * nv + 32 * cols - 1) / (32 * cols)) * 32 + 64;
+}
+
+// Ring shapes: R z rows per slot (one bulk copy per component plane moves R
+// rows) and D >= 2 slots.  Bandwidth depends mostly on the contiguous bytes
+// each bulk copy moves per component plane (R rows of nv values) times the
+// resident CTAs: ~1 KB per copy reaches about 40% of HBM peak, 2 KB with two
+// CTAs or 4 KB with one about 95% (measured on GB300).
+std::vector<RingChoice> ring_choices(int scheme, int precision, int nv, int stage, bool batched,
+                                     bool* query_failed) {
+  std::vector<RingChoice> out;
+  *query_failed = false;
+  const int header = stage_traits(scheme, precision, stage).header;
+  const int block = stage_block(scheme, precision, nv, stage);
+  for (int R = 1; R <= 32; R *= 2) {
+    const int slot = slot_bytes_of(precision, nv, stage, R);
+    for (int D = 2; D <= kMaxRing; ++D) {
+      // Consumer warps drift apart by at most D * R rows; the moment-slot
+      // barriers stay unambiguous only while that is <= kMomSlots - 2.
+      if (D * R > kMomSlots - 2) break;
+      const size_t smem = (size_t)header + (size_t)D * slot;
+      if (smem > (size_t)kStageSmemLimit) break;
+      const int occ = max_blocks(scheme, precision, stage, batched, block, smem);
+      if (occ < 0) {
+        *query_failed = true;
+        return {};
       }
+      if (occ == 0) continue;
+      RingChoice c;
+      c.rows_per_slot = R;
+      c.ring = D;
+      c.slot_bytes = slot;
+      c.occ = occ;
+      c.smem = smem;
+      c.score = std::min<int64_t>((int64_t)R * nv * 4 * occ, 4096);
+      out.push_back(c);
     }
-    if (best_d == 0) return fail(h, COSENU_EINVAL, "grid row does not fit in shared memory");
-    c.ring = best_d;
-    c.rows_per_slot = best_r;
-    c.slot_bytes = slot_bytes(h, s, best_r);
-    c.smem = (size_t)tr.header + (size_t)best_d * c.slot_bytes;
-    const int64_t max_grid = (int64_t)nsm * best_occ;
-    int64_t grid = (h->nz + kMinRowsPerCta - 1) / kMinRowsPerCta;
-    if (grid > max_grid) grid = max_grid;
-    if (grid < 1) grid = 1;
-    c.rows = (h->nz + grid - 1) / grid;
-    c.grid = (int)((h->nz + c.rows - 1) / c.rows);
-    h->cfg[s] = c;
   }
-  return COSENU_OK;
+  std::stable_sort(out.begin(), out.end(), [](const RingChoice& x, const RingChoice& y) {
+    if (x.score != y.score) return x.score > y.score;
+    if (x.occ != y.occ) return x.occ > y.occ;
+    return x.ring > y.ring;
+  });
+  return out;
 }
 
-StageArgs stage_args(cosenu_t h, int stage, int ycur) {
+cudaError_t launch_stage_kernel(int scheme, int precision, int stage, const StageArgs& a,
+                                const BatchTable* bt, int grid, int block, size_t smem,
+                                cudaStream_t stream) {
+  if (!bt && !stage_args_complete(precision, stage, a)) return cudaErrorInvalidValue;
+  if (scheme == COSENU_FDKO && precision == COSENU_FP64)
+    return launch_rk4_stage<kFDKO, kFP64>(stage, a, bt, grid, block, smem, stream);
+  if (scheme == COSENU_FDKO)
+    return launch_rk4_stage<kFDKO, kMIXED>(stage, a, bt, grid, block, smem, stream);
+  if (precision == COSENU_FP64)
+    return launch_rk4_stage<kWENO7, kFP64>(stage, a, bt, grid, block, smem, stream);
+  return launch_rk4_stage<kWENO7, kMIXED>(stage, a, bt, grid, block, smem, stream);
+}
+
+StageArgs stage_args(const cosenu_s* h, int stage, int ycur) {
   StageArgs a;
   std::memset(&a, 0, sizeof(a));
   a.nz = h->nz;
@@ -289,6 +284,10 @@ StageArgs stage_args(cosenu_t h, int stage, int ycur) {
   }
   return a;
 }
+
+}  // namespace cosenu
+
+namespace {
 
 cudaError_t take_event(cosenu_t h, cudaEvent_t* out) {
   if (!h->ev_free.empty()) {
@@ -332,9 +331,6 @@ cudaError_t enqueue_step(cosenu_t h, int ycur) {
   return cudaSuccess;
 }
 
-// The state buffer that follows a step from `ycur` (the mixed path updates in place).
-int next_y(cosenu_t h, int ycur) { return h->precision == COSENU_FP64 ? ycur ^ 1 : ycur; }
-
 void drop_graph(cosenu_t h) {
   if (h->graph) cudaGraphExecDestroy(h->graph);
   h->graph = nullptr;
@@ -375,7 +371,7 @@ void default_params(cosenu_t h) {
 }
 
 cosenu_t create_common(int64_t nz, int32_t nv, double L, int scheme, int precision,
-                       void* workspace, size_t ws_bytes) {
+                       void* workspace, size_t ws_bytes, cudaStream_t stream = nullptr) {
   if (!valid_sizes(nz, nv, scheme, precision) || !(L > 0.0) || !std::isfinite(L)) {
     fail(nullptr, COSENU_EINVAL,
          "invalid grid: need nz >= 1, 4 <= nv <= 256, nv % 4 == 0, L > 0, known scheme/precision");
@@ -414,9 +410,15 @@ cosenu_t create_common(int64_t nz, int32_t nv, double L, int scheme, int precisi
     }
     h->own_mem = true;
   }
-  cudaError_t e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
-  if (e != cudaSuccess) return bail(std::string("stream: ") + cudaGetErrorString(e), COSENU_ECUDA);
-  h->own_stream = true;
+  cudaError_t e = cudaSuccess;
+  if (stream) {
+    h->stream = stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess)
+      return bail(std::string("stream: ") + cudaGetErrorString(e), COSENU_ECUDA);
+    h->own_stream = true;
+  }
   h->y[0] = reinterpret_cast<double*>(h->ws + h->lay.y0);
   if (precision == COSENU_FP64)
     h->y[1] = reinterpret_cast<double*>(h->ws + h->lay.y1);
@@ -477,6 +479,30 @@ cosenu_t cosenu_create_external(int64_t nz, int32_t nv, double L, int scheme, in
 
 void cosenu_destroy(cosenu_t h) {
   if (!h) return;
+  if (h->in_batch) {
+    fail(nullptr, COSENU_EINVAL, "cosenu_destroy: the handle belongs to a batch (cosenu_batch_remove)");
+    return;
+  }
+  destroy_member(h);
+}
+
+}  // extern "C"
+
+namespace cosenu {
+
+cosenu_t create_member(int64_t nz, int32_t nv, double L, int scheme, int precision,
+                       cudaStream_t stream) {
+  if (!stream) {
+    fail(nullptr, COSENU_EINVAL, "create_member: NULL stream");
+    return nullptr;
+  }
+  cosenu_t h = create_common(nz, nv, L, scheme, precision, nullptr, 0, stream);
+  if (h) h->in_batch = true;
+  return h;
+}
+
+void destroy_member(cosenu_t h) {
+  if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
   drop_graph(h);
   for (int s = 1; s <= 5; ++s)
@@ -490,6 +516,10 @@ void cosenu_destroy(cosenu_t h) {
   delete h;
 }
 
+}  // namespace cosenu
+
+extern "C" {
+
 int cosenu_set_params(cosenu_t h, const cosenu_params* p) {
   if (!h || !p) return fail(h, COSENU_EINVAL, "NULL argument");
   const double vals[7] = {p->mu, p->omega, p->theta, p->lambda, p->ko_eps, p->weno_eps, p->dt};
@@ -499,6 +529,7 @@ int cosenu_set_params(cosenu_t h, const cosenu_params* p) {
   if (p->ko_eps < 0.0) return fail(h, COSENU_EINVAL, "ko_eps must be non-negative");
   h->p = *p;
   if (h->p.dt <= 0.0) h->p.dt = 0.4 * h->L / (double)h->nz;
+  ++h->version;
   drop_graph(h);
   return COSENU_OK;
 }
@@ -511,6 +542,7 @@ int cosenu_get_params(cosenu_t h, cosenu_params* p) {
 
 int cosenu_set_stream(cosenu_t h, void* stream) {
   if (!h) return fail(h, COSENU_EINVAL, "NULL handle");
+  if (h->in_batch) return fail(h, COSENU_EINVAL, "a batch member uses the batch's stream");
   CK(h, cudaStreamSynchronize(h->stream));
   drop_graph(h);
   if (h->own_stream) cudaStreamDestroy(h->stream);

@@ -56,6 +56,22 @@ __global__ void y32_from_y_kernel(const double* __restrict__ y, float* __restric
     y32[e] = d2f_rn_int(y[e]);
 }
 
+// y[0..3] += dy (in double), returns false if a result is not finite, and
+// writes the float copy of the four results.
+__device__ __forceinline__ bool apply4(double2* __restrict__ y, float4* __restrict__ y32,
+                                       float4 d) {
+  double2 a = y[0];
+  double2 b = y[1];
+  a.x += f2d_int(d.x);
+  a.y += f2d_int(d.y);
+  b.x += f2d_int(d.z);
+  b.y += f2d_int(d.w);
+  y[0] = a;
+  y[1] = b;
+  *y32 = make_float4(d2f_rn_int(a.x), d2f_rn_int(a.y), d2f_rn_int(b.x), d2f_rn_int(b.y));
+  return is_finite_bits(a.x) && is_finite_bits(a.y) && is_finite_bits(b.x) && is_finite_bits(b.y);
+}
+
 // Mixed path, end of an RK4 step: y <- y + dy in double (dy is the float
 // increment written by stage 4) and the float copy y32 <- round(y), in place,
 // element by element.  n = 8 nz nv (a multiple of 4).
@@ -66,24 +82,46 @@ __global__ void __launch_bounds__(256) apply_increment_kernel(double* __restrict
   bool bad = false;
   const int64_t n4 = n >> 2;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const float4 d = reinterpret_cast<const float4*>(dy)[i];
-    double2 a = reinterpret_cast<double2*>(y)[2 * i];
-    double2 b = reinterpret_cast<double2*>(y)[2 * i + 1];
-    a.x += f2d_int(d.x);
-    a.y += f2d_int(d.y);
-    b.x += f2d_int(d.z);
-    b.y += f2d_int(d.w);
-    bad |= !(is_finite_bits(a.x) && is_finite_bits(a.y) && is_finite_bits(b.x) &&
-             is_finite_bits(b.y));
-    reinterpret_cast<double2*>(y)[2 * i] = a;
-    reinterpret_cast<double2*>(y)[2 * i + 1] = b;
-    reinterpret_cast<float4*>(y32)[i] =
-        make_float4(d2f_rn_int(a.x), d2f_rn_int(a.y), d2f_rn_int(b.x), d2f_rn_int(b.y));
-  }
+       i += (int64_t)gridDim.x * blockDim.x)
+    bad |= !apply4(reinterpret_cast<double2*>(y) + 2 * i, reinterpret_cast<float4*>(y32) + i,
+                   reinterpret_cast<const float4*>(dy)[i]);
   if (__ballot_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, kErrNonFinite);
 }
 
+// The same update for several states: segment k is cut into chunks of
+// kApplyChunk4 float4 groups, chunks chunk_first[k] .. chunk_first[k + 1] - 1
+// of the launch; blocks walk the chunks.  Non-finite results are reported in
+// the segment's own error word.
+__global__ void __launch_bounds__(256) apply_increment_batch_kernel(
+    const ApplySeg* __restrict__ segs, const int64_t* __restrict__ chunk_first, int nseg,
+    int64_t nchunks) {
+  for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    int lo = 0, hi = nseg - 1;  // last segment whose first chunk is <= ch
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (chunk_first[mid] <= ch) lo = mid; else hi = mid - 1;
+    }
+    const ApplySeg sg = segs[lo];
+    const int64_t i0 = (ch - chunk_first[lo]) * kApplyChunk4;
+    const int64_t i1 = min(sg.n4, i0 + kApplyChunk4);
+    bool bad = false;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x)
+      bad |= !apply4(reinterpret_cast<double2*>(sg.y) + 2 * i,
+                     reinterpret_cast<float4*>(sg.y32) + i,
+                     reinterpret_cast<const float4*>(sg.dy)[i]);
+    if (__ballot_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0)
+      atomicOr(sg.err, kErrNonFinite);
+  }
+}
+
+// out[k] = *flags[k] (the error words of n handles); clears them if `clear`.
+__global__ void gather_flags_kernel(uint32_t* const* __restrict__ flags, int n,
+                                    uint32_t* __restrict__ out, int clear) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+    out[k] = *flags[k];
+    if (clear) *flags[k] = 0u;
+  }
+}
 
 // Column sums over z: out[q][v] = (1/nz) sum_z y[q][z][v].  Block = (q, 32 v);
 // 8 warps split z, partial sums combined in a fixed order.

@@ -8,6 +8,16 @@ namespace cosenu {
 
 constexpr int kDiagBlock = 256;
 constexpr int kDiagMaxBlocks = 1024;
+constexpr int64_t kApplyChunk4 = 1024;  // float4 groups per chunk of the batched increment
+
+// One state of the batched increment kernel: n4 = 2 nz nv float4 groups.
+struct ApplySeg {
+  double* y;
+  float* y32;
+  const float* dy;
+  int64_t n4;
+  uint32_t* err;
+};
 
 __global__ void ymoments_kernel(const double* __restrict__ y, int64_t nz, int nv,
                                 double* __restrict__ out, int stride);
@@ -15,6 +25,11 @@ __global__ void y32_from_y_kernel(const double* __restrict__ y, float* __restric
                                   int64_t n);
 __global__ void apply_increment_kernel(double* __restrict__ y, float* __restrict__ y32,
                                        const float* __restrict__ dy, int64_t n, uint32_t* err);
+__global__ void apply_increment_batch_kernel(const ApplySeg* __restrict__ segs,
+                                             const int64_t* __restrict__ chunk_first, int nseg,
+                                             int64_t nchunks);
+__global__ void gather_flags_kernel(uint32_t* const* __restrict__ flags, int n,
+                                    uint32_t* __restrict__ out, int clear);
 __global__ void zavg_kernel(const double* __restrict__ y, int64_t nz, int nv,
                             double* __restrict__ out);
 __global__ void conserved_partial_kernel(const double* __restrict__ y, int64_t nz, int nv,

@@ -269,543 +269,40 @@ __host__ __device__ constexpr int stage_smem_header_bytes() {
   return SmemHeader<PREC, stage_max_consumer_warps<SCHEME, PREC, STAGE>()>::kBytes;
 }
 
-template <int SCHEME, int PREC, int STAGE>
+
+// A z range of one grid of a batched launch.
+struct WorkItem {
+  int32_t inst;  // index into BatchTable::inst
+  int32_t pad;
+  int64_t z_begin, z_end;
+};
+
+// Work of a batched launch: CTA b advances rows [items[b].z_begin, items[b].z_end)
+// of grid inst[items[b].inst].  Every entry of `inst` carries the launch shape
+// (nv, ncols, ring, rows_per_slot, slot_bytes) of the launch.
+struct BatchTable {
+  const StageArgs* inst;
+  const WorkItem* items;
+};
+
+// The fused stage kernel.  Single grid (BATCHED = false): CTA b owns rows
+// [b * a.rows_per_cta, (b + 1) * a.rows_per_cta) of the grid in `a`.  Batched:
+// CTA b runs work item b of `bt` (`a` is unused), so grids of any sizes, with
+// their own parameters, share one launch; every cell sees the same arithmetic
+// as in a single-grid launch.
+template <int SCHEME, int PREC, int STAGE, bool BATCHED>
 __global__ void __launch_bounds__(stage_max_threads<SCHEME, PREC, STAGE>())
-    rk4_stage_kernel(const StageArgs a) {
-  using Real = typename Prec<PREC>::Real;
-  using Delta = typename Prec<PREC>::Delta;
-  using Acc = Real;
-  constexpr int NW = stage_max_consumer_warps<SCHEME, PREC, STAGE>();
-  using H = SmemHeader<PREC, NW>;
-  constexpr int LAG = Scheme<SCHEME>::kLag;
-  constexpr int WIN = Scheme<SCHEME>::kWin;
-  constexpr int LO = Scheme<SCHEME>::kLo;
-  constexpr int HI = Scheme<SCHEME>::kHi;
-  constexpr int MS = kMomSlots;
-
-  extern __shared__ __align__(128) unsigned char smem[];
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + H::kFlags);
-  Acc* part = reinterpret_cast<Acc*>(smem + H::kPart);      // [MS][NW][8]
-  Acc* partdy = reinterpret_cast<Acc*>(smem + H::kPartDy);  // [MS][NW][8]
-  Acc* momf = reinterpret_cast<Acc*>(smem + H::kMomf);      // [MS][8]
-  double* myring = reinterpret_cast<double*>(smem + H::kMyRing);  // [MS][8]
-  unsigned char* ring = smem + H::kBytes;
-
-  const int tid = threadIdx.x;
-  const int lane = tid & 31;
-  const int warp = tid >> 5;
-  constexpr int COLS = stage_cols<SCHEME, PREC, STAGE>();
-  const int ncw = (a.ncols + 32 * COLS - 1) / (32 * COLS);  // consumer warps; then producer, reducer
-  const int64_t nz = a.nz;
-  const int nv = a.nv;
-  const int R = a.rows_per_slot;
-  const SlotLayout L = slot_layout<PREC>(nv, STAGE, R);
-  const int D = a.ring;
-
-  const int64_t z_begin = (int64_t)blockIdx.x * a.rows_per_cta;
-  const int64_t z_end = min(nz, z_begin + a.rows_per_cta);
-  if (z_begin >= z_end) return;  // uniform over the CTA
-  const int64_t i_first = z_begin - LO;
-  const int64_t nrows = (z_end + HI) - i_first;
-  const int64_t ncent = z_end - z_begin;
-
-  const uint32_t bar0 = smem_addr(smem + H::kBars);
-  auto full_bar = [&](int k) { return bar0 + 8u * k; };
-  auto empty_bar = [&](int k) { return bar0 + 8u * (kMaxRing + k); };
-  auto part_bar = [&](int m) { return bar0 + 8u * (2 * kMaxRing + m); };
-  auto mom_bar = [&](int m) { return bar0 + 8u * (2 * kMaxRing + MS + m); };
-  auto dy_bar = [&](int m) { return bar0 + 8u * (2 * kMaxRing + 2 * MS + m); };
-
-  // Every lane waits (so each observes the phase), and the warp leaves together.
-  auto warp_wait = [&](uint32_t bar, uint32_t parity) {
-    const bool ok = mbar_wait_or_abort(bar, parity, abort_flag, a.err);
-    return __all_sync(0xffffffffu, ok);
-  };
-
-  if (tid == 0) {
-    for (int k = 0; k < kMaxRing; ++k) {
-      mbar_init(full_bar(k), 1);
-      mbar_init(empty_bar(k), ncw);
-    }
-    for (int m = 0; m < MS; ++m) {
-      mbar_init(part_bar(m), ncw);
-      mbar_init(mom_bar(m), 1);
-      mbar_init(dy_bar(m), ncw);
-    }
-    *abort_flag = 0;
-    fence_barrier_init();
-  }
-  __syncthreads();  // the only CTA-wide barrier
-
-  // =================================================================== producer
-  if (warp == ncw) {
-    if (lane != 0) return;
-    using WinY = typename Prec<PREC>::WinY;
-    const uint32_t rw = nv * sizeof(WinY), ry = nv * sizeof(double), rd = nv * sizeof(Delta);
-    const WinY* ywin = (PREC == kMIXED) ? reinterpret_cast<const WinY*>(a.y32_in)
-                                        : reinterpret_cast<const WinY*>(a.y_in);
-    const Delta* din = static_cast<const Delta*>(a.d_in);
-    const Delta* d1 = static_cast<const Delta*>(a.d1);
-    const Delta* d2 = static_cast<const Delta*>(a.d2);
-    const int64_t nslots = (nrows + R - 1) / R;
-    const int64_t plane = nz * nv;
-    int64_t issued = 0;
-    int slot = 0;
-    uint32_t fill = 0;  // how many times this slot has been filled before
-    for (int64_t j = 0; j < nslots; ++j) {
-      if (fill > 0 && !mbar_wait_or_abort(empty_bar(slot), (fill - 1) & 1u, abort_flag, a.err))
-        break;
-      fence_proxy_async();
-      const uint32_t bar = full_bar(slot);
-      const uint32_t base = smem_addr(ring + (size_t)slot * a.slot_bytes);
-      const int64_t i0 = i_first + j * R;  // first leading row of the slot
-      const int nr = (int)min((int64_t)R, nrows - j * R);
-      const bool contiguous = i0 >= 0 && i0 + nr <= nz;  // no periodic wrap inside
-      // center rows c = i - lag of this slot that lie in the CTA's range (stage 4)
-      const int64_t c0 = i0 - LAG;
-      const int64_t cl = max(c0, z_begin), ch = min(c0 + nr, z_end);
-      const int ncen = (STAGE == 4 && ch > cl) ? (int)(ch - cl) : 0;
-      // leading rows in the CTA's range (running moments of y, mixed)
-      const int64_t il = max(i0, z_begin), ih = min(i0 + nr, z_end);
-      const int nmy = (PREC == kMIXED && ih > il) ? (int)(ih - il) : 0;
-      uint32_t tx = nr * (8 * rw + (STAGE > 1 ? 8 * rd : 0));
-      tx += ncen * ((PREC == kFP64 ? 8 * ry : 0) + 16 * rd);
-      tx += nmy * 64;
-      mbar_arrive_expect_tx(bar, tx);
-#pragma unroll 1
-      for (int q = 0; q < 8; ++q) {
-        const uint32_t dw = base + L.y_off + q * R * rw;
-        const uint32_t dd = base + L.din_off + q * R * rd;
-        if (contiguous) {
-          bulk_g2s(dw, ywin + q * plane + i0 * nv, nr * rw, bar);
-          if (STAGE > 1) bulk_g2s(dd, din + q * plane + i0 * nv, nr * rd, bar);
-        } else {
-          for (int r = 0; r < nr; ++r) {
-            const int64_t row = wrap_row(i0 + r, nz);
-            bulk_g2s(dw + r * rw, ywin + q * plane + row * nv, rw, bar);
-            if (STAGE > 1) bulk_g2s(dd + r * rd, din + q * plane + row * nv, rd, bar);
-          }
-        }
-        if (ncen > 0) {
-          const int off = (int)(cl - c0);
-          const int64_t o = q * plane + cl * nv;
-          if (PREC == kFP64)
-            bulk_g2s(base + L.yc_off + (q * R + off) * ry, a.y_in + o, ncen * ry, bar);
-          bulk_g2s(base + L.d1c_off + (q * R + off) * rd, d1 + o, ncen * rd, bar);
-          bulk_g2s(base + L.d2c_off + (q * R + off) * rd, d2 + o, ncen * rd, bar);
-        }
-      }
-      if (nmy > 0) bulk_g2s(base + L.my_off + (int)(il - i0) * 64, a.my + il * 8, nmy * 64, bar);
-      issued = j + 1;
-      if (++slot == D) {
-        slot = 0;
-        ++fill;
-      }
-    }
-    // Leave only after the last fill of every slot has landed (each wait bounded).
-    for (int64_t j = (issued > D ? issued - D : 0); j < issued; ++j)
-      mbar_wait_bounded(full_bar((int)(j % D)), (uint32_t)((j / D) & 1));
-    return;
-  }
-
-  // =================================================================== reducer
-  if (warp == ncw + 1) {
-    // mixed stage 4: advance the running moments of y by the increment's moments
-    auto finish_dy = [&](int64_t rc, double my_row) {
-      const int m = (int)(rc % MS);
-      if (!warp_wait(dy_bar(m), (uint32_t)((rc / MS) & 1))) return false;
-      if (lane < 6) {
-        Acc acc = Acc(0);
-        for (int w = 0; w < ncw; ++w) acc += partdy[(m * NW + w) * 8 + lane];
-        a.my[(z_begin + rc) * 8 + lane] = my_row + double(acc);
-      }
-      return true;
-    };
-    double my_prev = 0.0;  // running y-moment (lane k) of the previous row
-    for (int64_t rc = 0; rc < ncent; ++rc) {
-      const int m = (int)(rc % MS);
-      if (!warp_wait(part_bar(m), (uint32_t)((rc / MS) & 1))) return;
-      double my_cur = 0.0;
-      if (lane < 6) {
-        Acc acc = Acc(0);
-        if (PREC == kFP64 || STAGE > 1)
-          for (int w = 0; w < ncw; ++w) acc += part[(m * NW + w) * 8 + lane];
-        if (PREC == kMIXED) {
-          my_cur = myring[m * 8 + lane];
-          momf[m * 8 + lane] = Acc(my_cur + double(acc));
-        } else {
-          momf[m * 8 + lane] = acc;
-        }
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(mom_bar(m));
-      if (PREC == kMIXED && STAGE == 4 && rc > 0 && !finish_dy(rc - 1, my_prev)) return;
-      my_prev = my_cur;
-    }
-    if (PREC == kMIXED && STAGE == 4 && ncent > 0) finish_dy(ncent - 1, my_prev);
-    return;
-  }
-
-  // =================================================================== consumers
-  // Thread t owns the COLS adjacent columns 2t.. of one species (nv is a
-  // multiple of 4, so the pair never straddles the species boundary).
-  const int col0 = tid * COLS;
-  const bool active = col0 < a.ncols;
-  const int s = active ? col0 / nv : 0;  // species
-  const int vj0 = active ? col0 % nv : 0;
-  const double dv = 2.0 / nv;
-  const double sgn = (s == 0) ? 1.0 : -1.0;
-  Real v[COLS], w3[COLS], w3v[COLS], wi[COLS], wiv[COLS], c_fd[COLS], eps_v[COLS];
-  bool upwind_left[COLS];
-#pragma unroll
-  for (int cc = 0; cc < COLS; ++cc) {
-    const double vd = -1.0 + (vj0 + cc + 0.5) * dv;
-    v[cc] = Real(vd);
-    // moment weights: D3 and Dr take + for nu and - for nubar, Di takes + for both
-    w3[cc] = active ? Real(sgn * dv) : Real(0);
-    w3v[cc] = active ? Real(sgn * dv * vd) : Real(0);
-    wi[cc] = active ? Real(dv) : Real(0);
-    wiv[cc] = active ? Real(dv * vd) : Real(0);
-    c_fd[cc] = Real(-vd * a.inv_dz / 12.0);
-    eps_v[cc] = Real(a.weno_eps / (vd * vd));  // WENO_eps(v u) = v WENO_{eps/v^2}(u)
-    upwind_left[cc] = vd > 0.0;
-  }
-  // H = (hvac_d + sgn lambda + sgn mu (D3_0 - v D3_1), hvac_r + sgn mu (Dr_0 - v Dr_1),
-  //      mu (Di_0 - v Di_1)) for (H_ee - H_xx, Re H_ex, Im H_ex)
-  const Real hd0 = Real(a.hvac_d + sgn * a.lambda);
-  const Real hr0 = Real(a.hvac_r);
-  const Real mus = Real(sgn * a.mu);
-  const Real mu = Real(a.mu);
-  const Real c_ko = Real(-a.ko_eps * a.inv_dz / 16.0);
-  const Real inv_dz = Real(a.inv_dz);
-  const Real dt = Real(a.dt);
-  const int64_t plane = nz * nv;
-  const int rstride = R * nv;  // slot elements between component planes
-
-  // Sliding window of this thread's columns: u[k] holds one row.
-  Real u[WIN][4][COLS];
-#pragma unroll
-  for (int k = 0; k < WIN; ++k)
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int cc = 0; cc < COLS; ++cc) u[k][q][cc] = Real(0);
-  Real fprev[4][COLS];  // WENO flux at c - 1/2
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-#pragma unroll
-    for (int cc = 0; cc < COLS; ++cc) fprev[q][cc] = Real(0);
-  // mixed stage 4: raw delta_3 of the last lag+1 rows (the window holds y + delta_3)
-  Real dring[LAG + 1][4][COLS];
-#pragma unroll
-  for (int k = 0; k <= LAG; ++k)
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int cc = 0; cc < COLS; ++cc) dring[k][q][cc] = Real(0);
-  bool nonfinite = false;
-  bool stop = false;
-  int slot = 0;
-  int rin = 0;       // row within the current slot
-  uint32_t par = 0;  // phase parity of the current slot
-  Delta* dout = static_cast<Delta*>(a.d_out) + (int64_t)(s * 4) * plane + vj0;
-  double* yout = a.y_out + (int64_t)(s * 4) * plane + vj0;
-
-  constexpr bool RING = Scheme<SCHEME>::kRing;
-  auto row = [&](auto kc, int64_t j) {
-    // Ring: the entering row goes to u[K] and window row m (0 = oldest) sits at
-    // u[(K + 1 + m) % WIN].  Shift register: rows move down one place per
-    // iteration and the entering row goes to u[WIN - 1].
-    constexpr int K = RING ? decltype(kc)::value : WIN - 1;
-    constexpr int O = RING ? K + 1 : 0;
-    constexpr int W0 = (O + 0) % WIN, W1 = (O + 1) % WIN, W2 = (O + 2) % WIN,
-                  W3 = (O + 3) % WIN, W4 = (O + 4) % WIN, W5 = (O + 5) % WIN,
-                  W6 = (O + 6) % WIN, W7 = (O + 7) % WIN;
-    if (!RING) {
-#pragma unroll
-      for (int k = 0; k < WIN - 1; ++k)
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-          for (int cc = 0; cc < COLS; ++cc) u[k][q][cc] = u[k + 1][q][cc];
-    }
-    const int64_t i = i_first + j;
-    const int64_t c = i - LAG;
-    const int rl = (int)(i - z_begin);  // relative leading row
-    const int rc = rl - LAG;            // relative center row
-    const bool lead_in_range = rl >= 0 && i < z_end;
-    const bool center_in_range = rc >= 0 && c < z_end;
-    const unsigned char* sb = ring + (size_t)slot * a.slot_bytes;
-    const int ecol = (s * 4 * R + rin) * nv + vj0;  // component 0 of this row in the slot
-
-    if (rin == 0 && !warp_wait(full_bar(slot), par)) {
-      stop = true;
-      return;
-    }
-
-    // ---- read the slot: leading row i (window arrays), center row c (stage 4)
-    Real draw[4][COLS];
-    double yc[4][COLS];
-    Real e1[4][COLS], e2[4][COLS];
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int cc = 0; cc < COLS; ++cc) {
-        draw[q][cc] = Real(0);
-        yc[q][cc] = 0.0;
-        e1[q][cc] = e2[q][cc] = Real(0);
-      }
-    {
-      using WinY = typename Prec<PREC>::WinY;
-      const WinY* ys = reinterpret_cast<const WinY*>(sb + L.y_off);
-      const Delta* ds = reinterpret_cast<const Delta*>(sb + L.din_off);
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int e = ecol + q * rstride;
-        WinY yv[COLS];
-        Delta dd[COLS];
-#pragma unroll
-        for (int cc = 0; cc < COLS; ++cc) {
-          yv[cc] = WinY(0);
-          dd[cc] = Delta(0);
-        }
-        if (active) {
-          vload(ys + e, yv);
-          if (STAGE > 1) vload(ds + e, dd);
-        }
-#pragma unroll
-        for (int cc = 0; cc < COLS; ++cc) {
-          draw[q][cc] = Real(dd[cc]);
-          u[K][q][cc] = Real(yv[cc] + dd[cc]);  // fp64: y + delta; mixed: float(y) + delta
-        }
-      }
-      if (STAGE == 4 && center_in_range && active) {
-        const double* ycs = reinterpret_cast<const double*>(sb + L.yc_off);
-        const Delta* d1s = reinterpret_cast<const Delta*>(sb + L.d1c_off);
-        const Delta* d2s = reinterpret_cast<const Delta*>(sb + L.d2c_off);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int e = ecol + q * rstride;
-          Delta t1[COLS], t2[COLS];
-          if (PREC == kFP64) vload(ycs + e, yc[q]);
-          vload(d1s + e, t1);
-          vload(d2s + e, t2);
-#pragma unroll
-          for (int cc = 0; cc < COLS; ++cc) {
-            e1[q][cc] = Real(t1[cc]);
-            e2[q][cc] = Real(t2[cc]);
-          }
-        }
-      }
-      if (PREC == kMIXED && warp == 0 && lane < 6 && lead_in_range)
-        myring[(rl & (MS - 1)) * 8 + lane] =
-            reinterpret_cast<const double*>(sb + L.my_off + rin * 64)[lane];
-    }
-    if (PREC == kMIXED && STAGE == 4) {
-#pragma unroll
-      for (int k = 0; k < LAG; ++k)
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-          for (int cc = 0; cc < COLS; ++cc) dring[k][q][cc] = dring[k + 1][q][cc];
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int cc = 0; cc < COLS; ++cc) dring[LAG][q][cc] = draw[q][cc];
-    }
-    if (++rin == R) {  // the whole slot has been read: hand it back to the producer
-      __syncwarp();
-      if (lane == 0) mbar_arrive(empty_bar(slot));
-      rin = 0;
-      if (++slot == D) {
-        slot = 0;
-        par ^= 1u;
-      }
-    }
-
-    // ---- partial velocity moments of row i (finished by the reducer)
-    if (lead_in_range) {
-      const int m = rl & (MS - 1);
-      if (PREC == kFP64 || STAGE > 1) {
-        // fp64: moments of u itself; mixed: of the increment (y's are running sums)
-        Real m6[6] = {Real(0), Real(0), Real(0), Real(0), Real(0), Real(0)};
-#pragma unroll
-        for (int cc = 0; cc < COLS; ++cc) {
-          const Real s0 = (PREC == kFP64) ? u[K][0][cc] : draw[0][cc];
-          const Real s1 = (PREC == kFP64) ? u[K][1][cc] : draw[1][cc];
-          const Real s2 = (PREC == kFP64) ? u[K][2][cc] : draw[2][cc];
-          const Real s3 = (PREC == kFP64) ? u[K][3][cc] : draw[3][cc];
-          const Real t3 = s0 - s1;
-          m6[0] += w3[cc] * t3;
-          m6[1] += w3v[cc] * t3;
-          m6[2] += w3[cc] * s2;
-          m6[3] += w3v[cc] * s2;
-          m6[4] += wi[cc] * s3;
-          m6[5] += wiv[cc] * s3;
-        }
-        const Real tot = warp_sum6_transposed(m6);
-        const int k = (lane >> 2) & 7;
-        if ((lane & 3) == 0 && k < 6) part[(m * NW + warp) * 8 + k] = tot;
-      }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(part_bar(m));
-    }
-
-    // ---- center row c = i - lag
-    Real fcur[4][COLS];
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int cc = 0; cc < COLS; ++cc) fcur[q][cc] = Real(0);
-    if (SCHEME == kWENO7 && rc >= -1 && c < z_end) {
-      // flux F_{c+1/2} = v * WENO(u), upwind by the sign of v
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int cc = 0; cc < COLS; ++cc) {
-          Real r;
-          if (upwind_left[cc])
-            r = weno7_face(u[W0][q][cc], u[W1][q][cc], u[W2][q][cc], u[W3][q][cc], u[W4][q][cc],
-                           u[W5][q][cc], u[W6][q][cc], eps_v[cc]);
-          else
-            r = weno7_face(u[W7][q][cc], u[W6][q][cc], u[W5][q][cc], u[W4][q][cc], u[W3][q][cc],
-                           u[W2][q][cc], u[W1][q][cc], eps_v[cc]);
-          fcur[q][cc] = v[cc] * r;
-        }
-    }
-    if (center_in_range) {
-      const int m = rc & (MS - 1);
-      if (!warp_wait(mom_bar(m), (uint32_t)((rc / MS) & 1))) {
-        stop = true;
-        return;
-      }
-      const Acc* mf = momf + m * 8;
-      const Real D30 = Real(mf[0]), D31 = Real(mf[1]), Dr0 = Real(mf[2]), Dr1 = Real(mf[3]),
-                 Di0 = Real(mf[4]), Di1 = Real(mf[5]);
-      constexpr int CC = (SCHEME == kFDKO) ? W2 : W3;  // the center row in the window
-      const int64_t rowoff = c * nv;
-      Real kk[4][COLS];
-#pragma unroll
-      for (int cc = 0; cc < COLS; ++cc) {
-        const Real dH = hd0 + mus * (D30 - v[cc] * D31);
-        const Real hr = hr0 + mus * (Dr0 - v[cc] * Dr1);
-        const Real hi = mu * (Di0 - v[cc] * Di1);
-        const Real ua = u[CC][0][cc], ub = u[CC][1][cc], ucr = u[CC][2][cc], uci = u[CC][3][cc];
-        const Real amb = ua - ub;
-        // -i [H, rho] for 2x2 Hermitian matrices, Eq. (eom)
-        const Real adot = Real(2) * (hi * ucr - hr * uci);
-        kk[0][cc] = adot;
-        kk[1][cc] = -adot;
-        kk[2][cc] = dH * uci - amb * hi;
-        kk[3][cc] = -dH * ucr + amb * hr;
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          Real adv;
-          if (SCHEME == kFDKO) {
-            const Real um2 = u[W0][q][cc], um1 = u[W1][q][cc], u0 = u[W2][q][cc],
-                       up1 = u[W3][q][cc], up2 = u[W4][q][cc];
-            const Real fd = Real(8) * (up1 - um1) - (up2 - um2);
-            const Real ko = (um2 + up2) - Real(4) * (um1 + up1) + Real(6) * u0;
-            adv = c_fd[cc] * fd + c_ko * ko;
-          } else {
-            adv = -(fcur[q][cc] - fprev[q][cc]) * inv_dz;
-          }
-          kk[q][cc] += adv;
-        }
-      }
-      if (STAGE < 4) {
-        const Real f = (STAGE == 3) ? dt : Real(0.5) * dt;
-        if (active) {
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            Delta o[COLS];
-#pragma unroll
-            for (int cc = 0; cc < COLS; ++cc) o[cc] = Delta(f * kk[q][cc]);
-            vstore(dout + rowoff + (int64_t)q * plane, o);
-          }
-        }
-      } else {
-        Real incr[4][COLS];
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-#pragma unroll
-          for (int cc = 0; cc < COLS; ++cc) {
-            Real d3;
-            if (PREC == kFP64)
-              d3 = Real(double(u[CC][q][cc]) - yc[q][cc]);  // u = y + delta_3 at the center
-            else
-              d3 = dring[0][q][cc];
-            incr[q][cc] = (e1[q][cc] + Real(2) * e2[q][cc] + d3) * Real(1.0 / 3.0) +
-                          (dt * Real(1.0 / 6.0)) * kk[q][cc];
-          }
-        if (PREC == kFP64) {
-          bool bad = false;
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            double yn[COLS];
-#pragma unroll
-            for (int cc = 0; cc < COLS; ++cc) {
-              yn[cc] = yc[q][cc] + double(incr[q][cc]);
-              bad |= !is_finite_bits(yn[cc]);
-            }
-            if (active) vstore(yout + rowoff + (int64_t)q * plane, yn);
-          }
-          nonfinite |= bad;
-        } else {
-          // the float increment; apply_increment_kernel adds it to y in double
-          if (active) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              Delta o[COLS];
-#pragma unroll
-              for (int cc = 0; cc < COLS; ++cc) o[cc] = Delta(incr[q][cc]);
-              vstore(dout + rowoff + (int64_t)q * plane, o);
-            }
-          }
-          // float moments of the increment advance the FP64 running moments of y
-          Real m6[6] = {Real(0), Real(0), Real(0), Real(0), Real(0), Real(0)};
-#pragma unroll
-          for (int cc = 0; cc < COLS; ++cc) {
-            const Real t3 = incr[0][cc] - incr[1][cc];
-            m6[0] += w3[cc] * t3;
-            m6[1] += w3v[cc] * t3;
-            m6[2] += w3[cc] * incr[2][cc];
-            m6[3] += w3v[cc] * incr[2][cc];
-            m6[4] += wi[cc] * incr[3][cc];
-            m6[5] += wiv[cc] * incr[3][cc];
-          }
-          const Real tot = warp_sum6_transposed(m6);
-          const int k = (lane >> 2) & 7;
-          if ((lane & 3) == 0 && k < 6) partdy[(m * NW + warp) * 8 + k] = tot;
-          __syncwarp();
-          if (lane == 0) mbar_arrive(dy_bar(m));
-        }
-      }
-    }
-    if (SCHEME == kWENO7) {
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int cc = 0; cc < COLS; ++cc) fprev[q][cc] = fcur[q][cc];
-    }
-  };
-
-  if constexpr (RING) {
-#pragma unroll 1
-    for (int64_t jb = 0; jb < nrows && !stop; jb += WIN) {
-      static_for<0, WIN>([&](auto kc) {
-        const int64_t j = jb + decltype(kc)::value;
-        if (j < nrows && !stop) row(kc, j);
-      });
-    }
+    rk4_stage_kernel(const StageArgs a, const BatchTable bt) {
+  if constexpr (BATCHED) {
+    const WorkItem w = bt.items[blockIdx.x];
+    const StageArgs a = bt.inst[w.inst];  // this item's grid (shadows the unused launch block)
+    const int64_t z_begin = w.z_begin;
+    const int64_t z_end = w.z_end;
+#include "stage_body.inc"
   } else {
-#pragma unroll 1
-    for (int64_t j = 0; j < nrows && !stop; ++j) row(std::integral_constant<int, 0>{}, j);
-  }
-
-  if (STAGE == 4 && PREC == kFP64) {
-    const unsigned any = __ballot_sync(0xffffffffu, nonfinite);
-    if (lane == 0 && any) atomicOr(a.err, kErrNonFinite);
+    const int64_t z_begin = (int64_t)blockIdx.x * a.rows_per_cta;
+    const int64_t z_end = min(a.nz, z_begin + a.rows_per_cta);
+#include "stage_body.inc"
   }
 }
 

@@ -124,3 +124,30 @@ def collective_state_device(nz: int, nv: int, device, *, alpha=0.9, sigma_nu=0.6
         s[sp, 2] = cr[:, None]
         s[sp, 3] = ci[:, None]
     return s
+
+
+def batch_instances(n: int, *, seed=12866, nz_range=(1024, 32768), nv_choices=(32, 64, 128),
+                    mu_range=(0.1, 10.0), alpha_range=(0.7, 1.2), sigma_range=(0.3, 0.8),
+                    schemes=(0, 1), dz_mu=0.2, cfl=0.4):
+    """Parameters of n independent collective-oscillation grids for the batched
+    solver: nz log-uniform on nz_range, nv uniform over nv_choices, mu
+    log-uniform on mu_range, alpha and both sigmas uniform, scheme uniform over
+    `schemes`; dz = dz_mu / mu, L = nz dz, dt = cfl dz.  Each parameter draws
+    from its own uniform01 stream (seed + k); instance i's state seed is
+    seed + 1000 + i.  Returns a list of dicts."""
+    u = [uniform01(n, seed + k) for k in range(7)]
+    lo, hi = np.log(nz_range[0]), np.log(nz_range[1])
+    out = []
+    for i in range(n):
+        nz = int(np.floor(np.exp(lo + (hi - lo) * u[0][i])))
+        nv = int(nv_choices[min(int(u[1][i] * len(nv_choices)), len(nv_choices) - 1)])
+        mu = float(np.exp(np.log(mu_range[0]) + np.log(mu_range[1] / mu_range[0]) * u[2][i]))
+        alpha = alpha_range[0] + (alpha_range[1] - alpha_range[0]) * u[3][i]
+        s_nu = sigma_range[0] + (sigma_range[1] - sigma_range[0]) * u[4][i]
+        s_nb = sigma_range[0] + (sigma_range[1] - sigma_range[0]) * u[5][i]
+        scheme = int(schemes[min(int(u[6][i] * len(schemes)), len(schemes) - 1)])
+        dz = dz_mu / mu
+        out.append({"nz": nz, "nv": nv, "mu": mu, "alpha": float(alpha), "sigma_nu": float(s_nu),
+                    "sigma_nubar": float(s_nb), "scheme": scheme, "L": nz * dz, "dt": cfl * dz,
+                    "seed": seed + 1000 + i})
+    return out
