@@ -32,6 +32,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -355,6 +357,67 @@ def run_batched(args, device, hbm_peak):
         torch.cuda.empty_cache()
 
 
+SERVE_WORKLOAD = ("serving trace: Poisson arrivals, grids from the batched-run recipe, precision "
+                  "alternating mixed / FP64, t_final U[50, 500]/mu, 64 GB workspace budget")
+
+
+def serve_trace(b, trace, budget, rate_scale=1.0, max_running=0, precision=None):
+    """Submit the trace's runs at their arrival times (divided by rate_scale), wait for
+    all, and summarise time-to-solution (submission to result, queueing included)."""
+    srv = b.Server(budget, max_running=max_running)
+    try:
+        t0 = time.perf_counter()
+        tickets = []
+        for r in trace:
+            delay = t0 + r["t_arrival"] / rate_scale - time.perf_counter()
+            if delay > 0:
+                time.sleep(delay)
+            req = b.make_request(r["nz"], r["nv"], r["L"], r["scheme"],
+                                 r["precision"] if precision is None else precision,
+                                 nsteps=r["nsteps"], alpha=r["alpha"], sigma_nu=r["sigma_nu"],
+                                 sigma_nubar=r["sigma_nubar"], eps0=1e-6, seed=r["seed"],
+                                 mu=r["mu"], dt=r["dt"])
+            tickets.append(srv.submit(req))
+        res = [srv.wait(t, 3600.0)[1] for t in tickets]
+        st = srv.stats()
+    finally:
+        srv.close()
+    lat = sorted(r["t_done"] - r["t_submit"] for r in res)
+    span = max(r["t_done"] for r in res) - min(r["t_submit"] for r in res)
+    cu = sum(2 * r["nz"] * r["nv"] * r["nsteps"] for r in trace)
+    q = lambda p: float(np.percentile(lat, p))  # noqa: E731
+    return {"requests": len(trace), "offered_rate_per_s": len(trace) / (trace[-1]["t_arrival"] /
+                                                                         rate_scale),
+            "p50_s": q(50), "p99_s": q(99), "mean_s": float(np.mean(lat)), "max_s": lat[-1],
+            "makespan_s": span, "completed_per_s": len(trace) / span,
+            "cell_updates_per_s": cu / span, "statuses": sorted({r["status"] for r in res}),
+            "peak_workspace_bytes": st["peak_bytes"], "budget_bytes": st["budget"],
+            "rounds": st["rounds"], "max_running": max_running}
+
+
+def run_serving(args):
+    """Continuous batching on a Poisson trace, a second trace at 70% of the measured
+    capacity, and the first trace served one run at a time in FP64."""
+    from paper_2203_12866_gb300 import binding as b
+    from paper_2203_12866_gb300 import inputs
+
+    trace = inputs.serving_trace(args.serve_requests, args.serve_rate,
+                                 step_scale=args.serve_step_scale)
+    budget = 64 << 30
+    out = {"workload": SERVE_WORKLOAD, "rate_per_s": args.serve_rate,
+           "step_scale": args.serve_step_scale,
+           "steps_range": [min(r["nsteps"] for r in trace), max(r["nsteps"] for r in trace)],
+           "cell_updates": sum(2 * r["nz"] * r["nv"] * r["nsteps"] for r in trace)}
+    out["batched"] = serve_trace(b, trace, budget)
+    cap = out["batched"]["completed_per_s"]
+    scale = 0.7 * cap / args.serve_rate  # arrival times stretched to 70% of capacity
+    out["batched_70pct"] = serve_trace(b, trace, budget, rate_scale=scale)
+    if args.serve_fp64_baseline:
+        out["fp64_one_at_a_time"] = serve_trace(b, trace, budget, max_running=1,
+                                                precision=b.COSENU_FP64)
+    return out
+
+
 def run_ours(args, world, rank, local):
     import torch
 
@@ -464,6 +527,7 @@ def run_ours(args, world, rank, local):
     torch.cuda.empty_cache()
 
     batched = run_batched(args, device, hbm_peak) if args.batched else None
+    serving = run_serving(args) if args.serving and rank == 0 else None
 
     # ---- oracle on the host cores (rank 0, one GPU only)
     cpu = None
@@ -486,7 +550,7 @@ def run_ours(args, world, rank, local):
                        "l2": "inputs larger than L2 (state 17.2 GB >> 129 MB)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clk, "variants": variants, "batched": batched,
+            "clocks": clk, "variants": variants, "batched": batched, "serving": serving,
             "conserved_after": {"tr_nu": cons["tr_nu"], "M": list(cons["M"]),
                                 "dP_max": cons["dP_max"]},
         }
@@ -510,6 +574,13 @@ def main():
     ap.add_argument("--no-batched", dest="batched", action="store_false")
     ap.add_argument("--batch-n", type=int, default=256)
     ap.add_argument("--batch-steps", type=int, default=20)
+    ap.add_argument("--no-serving", dest="serving", action="store_false")
+    ap.add_argument("--serve-requests", type=int, default=32)
+    ap.add_argument("--serve-rate", type=float, default=50.0)
+    ap.add_argument("--serve-step-scale", type=float, default=0.05,
+                    help="fraction of each run's t_final simulated (1 = the full trace)")
+    ap.add_argument("--no-serve-fp64-baseline", dest="serve_fp64_baseline",
+                    action="store_false")
     ap.add_argument("--nz", type=int, default=NZ_FULL,
                     help="z cells (smaller values only for profiling captures)")
     args = ap.parse_args()

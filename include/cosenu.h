@@ -63,7 +63,9 @@ enum {
   COSENU_ENOMEM = -2,      /* device or host allocation failed */
   COSENU_ECUDA = -3,       /* a CUDA runtime call failed */
   COSENU_ENONFINITE = -4,  /* a non-finite value appeared in the state */
-  COSENU_ETIMEOUT = -5     /* a bounded device-side wait gave up */
+  COSENU_ETIMEOUT = -5,    /* a bounded device-side wait gave up */
+  COSENU_ECANCELLED = -6,  /* a served run was cancelled */
+  COSENU_PENDING = 1       /* a served run has not finished yet (not an error) */
 };
 
 /* Physical and numerical parameters (Sec. 2 and 3).
@@ -131,6 +133,19 @@ int cosenu_set_state(cosenu_t h, const double* host, size_t n);
 
 /* Same from a device buffer of n doubles (stream-ordered, asynchronous). */
 int cosenu_set_state_device(cosenu_t h, const double* dev, size_t n);
+
+/* Set the initial state of the collective-oscillation runs of Sec. 5, built on
+ * the device, and reset the step counter (waits):
+ *   S_ee(z, v)    = g_nu(v),  Sbar_ee(z, v) = alpha g_nubar(v),  S_xx = Sbar_xx = 0,
+ *   S_ex = Sbar_ex = eps0 exp(i phi(z)),
+ * with g(v) proportional to exp(-(v - 1)^2 / (2 sigma^2)) at the bin midpoints,
+ * normalised so that sum_j dv g(v_j) = 1, and the random phase
+ * phi(z_i) = 2 pi u_i, u_i = (splitmix64(i XOR seed) >> 11) 2^-53 (splitmix64:
+ * x += 0x9E3779B97F4A7C15; x = (x ^ x >> 30) * 0xBF58476D1CE4E5B9;
+ * x = (x ^ x >> 27) * 0x94D049BB133111EB; x ^= x >> 31).
+ * sigma_nu, sigma_nubar > 0; alpha, eps0 finite. */
+int cosenu_set_state_collective(cosenu_t h, double alpha, double sigma_nu, double sigma_nubar,
+                                double eps0, uint64_t seed);
 
 /* Copy the current state to a host buffer of n = 8 nz nv doubles (waits). */
 int cosenu_get_state(cosenu_t h, double* host, size_t n);
@@ -283,6 +298,87 @@ void* cosenu_batch_stream(cosenu_batch_t b);
 
 /* Description of the last error of b (of this thread for b = NULL). */
 const char* cosenu_batch_last_error(cosenu_batch_t b);
+
+/* ------------------------------------------------------------------------
+ * Serving: independent runs queued by any thread and executed by one batched
+ * solver on the current device, under a device-memory budget (continuous
+ * batching).  A worker thread repeats rounds: admit queued runs oldest first
+ * while their workspaces (cosenu_workspace_bytes) fit in the budget and the
+ * member limit allows -- the first that does not fit stops admission, so no
+ * run is overtaken; set up each admitted run (member grid, parameters,
+ * initial state); advance the batch by the fewest steps any run still needs,
+ * capped at the round length; then retire the runs that reached their step
+ * count or raised an error flag (diagnostics, optional copy of the final
+ * state, device memory released).  A run's results are bit-identical to the
+ * same grid stepped alone.  The calls below are thread-safe.
+ */
+typedef struct cosenu_server_s* cosenu_server_t;
+
+/* One run.  state: host initial state [2][4][nz][nv], or NULL for the
+ * collective initial state of cosenu_set_state_collective with the fields
+ * alpha..seed.  out_state: host buffer of 8 nz nv doubles that receives the
+ * final state, or NULL.  Both pointers must stay valid until the run has
+ * finished (cosenu_poll / cosenu_wait returned 0) or was cancelled. */
+typedef struct {
+  int64_t nz;
+  int32_t nv;
+  double L;
+  int32_t scheme, precision;
+  cosenu_params params;  /* dt <= 0: the default 0.4 dz */
+  int64_t nsteps;        /* RK4 steps to take (>= 0) */
+  const double* state;
+  double alpha, sigma_nu, sigma_nubar, eps0;
+  uint64_t seed;
+  double* out_state;
+} cosenu_request;
+
+/* Outcome of a run.  status: 0, COSENU_PENDING (not finished), or the run's
+ * error (COSENU_ENONFINITE, COSENU_ETIMEOUT, COSENU_ECANCELLED, ...).
+ * conserved: diagnostics of the final state (status 0).  Times in seconds
+ * since the server was created (t_admit, t_done < 0 until they happen). */
+typedef struct {
+  int32_t status;
+  int64_t steps;
+  cosenu_conserved_t conserved;
+  double t_submit, t_admit, t_done;
+} cosenu_result;
+
+typedef struct {
+  int64_t submitted, admitted, finished, rounds, steps;
+  int32_t queued, running;
+  size_t bytes_in_use, peak_bytes, budget;  /* member workspaces */
+} cosenu_server_stats;
+
+/* budget_bytes: device memory the runs' workspaces may hold together (the
+ * batch's launch tables, about 0.5 KB per run, come on top); max_running:
+ * most runs in the batch at once (0 = no limit); round_steps: most steps per
+ * round (0 = 64).  NULL on failure (cosenu_server_last_error(NULL)). */
+cosenu_server_t cosenu_server_create(size_t budget_bytes, int32_t max_running,
+                                     int32_t round_steps);
+
+/* Stop the worker after its current round; runs not finished are cancelled. */
+void cosenu_server_destroy(cosenu_server_t s);
+
+/* Queue a run; *ticket identifies it.  COSENU_ENOMEM if its workspace alone
+ * exceeds the budget, COSENU_EINVAL for an invalid request. */
+int cosenu_submit(cosenu_server_t s, const cosenu_request* r, uint64_t* ticket);
+
+/* COSENU_PENDING while the run is queued or running (*out shows its progress);
+ * 0 once it has finished: *out receives the result and the ticket is released.
+ * COSENU_EINVAL for an unknown (or already collected) ticket. */
+int cosenu_poll(cosenu_server_t s, uint64_t ticket, cosenu_result* out);
+
+/* Like cosenu_poll, but waits up to timeout_s seconds (< 0: no limit). */
+int cosenu_wait(cosenu_server_t s, uint64_t ticket, double timeout_s, cosenu_result* out);
+
+/* Cancel a run: a queued run is dropped, a running one leaves the batch at the
+ * end of the current round; its result has status COSENU_ECANCELLED. */
+int cosenu_cancel(cosenu_server_t s, uint64_t ticket);
+
+int cosenu_server_get_stats(cosenu_server_t s, cosenu_server_stats* out);
+
+/* Description of the last error of s (of this thread for s = NULL). */
+const char* cosenu_server_last_error(cosenu_server_t s);
 
 /* Conserved-quantity diagnostics without any device allocation.  (The paper has
  * no counterpart: this entry point exists for callers of this library.)

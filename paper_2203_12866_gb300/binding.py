@@ -19,12 +19,13 @@ COSENU_FDKO, COSENU_WENO7 = 0, 1
 COSENU_FP64, COSENU_MIXED = 0, 1
 COSENU_OK, COSENU_EINVAL, COSENU_ENOMEM, COSENU_ECUDA, COSENU_ENONFINITE, COSENU_ETIMEOUT = (
     0, -1, -2, -3, -4, -5)
+COSENU_ECANCELLED, COSENU_PENDING = -6, 1
 
 # Every entry point include/cosenu.h declares.
 EXPORTS = (
     "cosenu_create", "cosenu_workspace_bytes", "cosenu_create_external", "cosenu_destroy",
     "cosenu_set_params", "cosenu_get_params", "cosenu_set_stream", "cosenu_set_state",
-    "cosenu_set_state_device", "cosenu_get_state", "cosenu_get_rows", "cosenu_state_device",
+    "cosenu_set_state_device", "cosenu_set_state_collective", "cosenu_get_state", "cosenu_get_rows", "cosenu_state_device",
     "cosenu_step",
     "cosenu_sync", "cosenu_moments", "cosenu_conserved", "cosenu_set_stage_timing",
     "cosenu_stage_times", "cosenu_steps_taken",
@@ -34,6 +35,8 @@ EXPORTS = (
     "cosenu_batch_member", "cosenu_batch_tune", "cosenu_batch_classes",
     "cosenu_batch_class_info", "cosenu_batch_set_stage_timing", "cosenu_batch_stage_times",
     "cosenu_batch_stream", "cosenu_batch_last_error",
+    "cosenu_server_create", "cosenu_server_destroy", "cosenu_submit", "cosenu_poll", "cosenu_wait",
+    "cosenu_cancel", "cosenu_server_get_stats", "cosenu_server_last_error",
     "cosenu_conserved_noalloc",
 )
 
@@ -57,6 +60,30 @@ class cosenu_batch_class(ctypes.Structure):
                 ("grid", ctypes.c_int32 * 4), ("smem", ctypes.c_int32 * 4),
                 ("occupancy", ctypes.c_int32 * 4), ("concurrent", ctypes.c_int32),
                 ("kernel_ms", ctypes.c_double * 5)]
+
+
+class cosenu_request(ctypes.Structure):
+    _fields_ = [("nz", ctypes.c_int64), ("nv", ctypes.c_int32), ("L", ctypes.c_double),
+                ("scheme", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("params", cosenu_params), ("nsteps", ctypes.c_int64),
+                ("state", ctypes.POINTER(ctypes.c_double)), ("alpha", ctypes.c_double),
+                ("sigma_nu", ctypes.c_double), ("sigma_nubar", ctypes.c_double),
+                ("eps0", ctypes.c_double), ("seed", ctypes.c_uint64),
+                ("out_state", ctypes.POINTER(ctypes.c_double))]
+
+
+class cosenu_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("steps", ctypes.c_int64),
+                ("conserved", cosenu_conserved_t), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+
+class cosenu_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64),
+                ("finished", ctypes.c_int64), ("rounds", ctypes.c_int64),
+                ("steps", ctypes.c_int64), ("queued", ctypes.c_int32),
+                ("running", ctypes.c_int32), ("bytes_in_use", ctypes.c_size_t),
+                ("peak_bytes", ctypes.c_size_t), ("budget", ctypes.c_size_t)]
 
 
 class CosenuError(RuntimeError):
@@ -89,6 +116,9 @@ def load(path: str = LIB_PATH):
         "cosenu_set_stream": (ctypes.c_int, [vp, vp]),
         "cosenu_set_state": (ctypes.c_int, [vp, dp, sz]),
         "cosenu_set_state_device": (ctypes.c_int, [vp, vp, sz]),
+        "cosenu_set_state_collective": (ctypes.c_int, [vp, ctypes.c_double, ctypes.c_double,
+                                                       ctypes.c_double, ctypes.c_double,
+                                                       ctypes.c_uint64]),
         "cosenu_get_state": (ctypes.c_int, [vp, dp, sz]),
         "cosenu_get_rows": (ctypes.c_int, [vp, i64, i64, dp]),
         "cosenu_state_device": (vp, [vp]),
@@ -119,6 +149,16 @@ def load(path: str = LIB_PATH):
         "cosenu_batch_set_stage_timing": (ctypes.c_int, [vp, ctypes.c_int]),
         "cosenu_batch_stage_times": (ctypes.c_int, [vp, dp, ctypes.POINTER(i64)]),
         "cosenu_batch_stream": (vp, [vp]),
+        "cosenu_server_create": (vp, [sz, i32, i32]),
+        "cosenu_server_destroy": (None, [vp]),
+        "cosenu_submit": (ctypes.c_int, [vp, ctypes.POINTER(cosenu_request),
+                                         ctypes.POINTER(ctypes.c_uint64)]),
+        "cosenu_poll": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.POINTER(cosenu_result)]),
+        "cosenu_wait": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_double,
+                                       ctypes.POINTER(cosenu_result)]),
+        "cosenu_cancel": (ctypes.c_int, [vp, ctypes.c_uint64]),
+        "cosenu_server_get_stats": (ctypes.c_int, [vp, ctypes.POINTER(cosenu_server_stats)]),
+        "cosenu_server_last_error": (ctypes.c_char_p, [vp]),
         "cosenu_batch_last_error": (ctypes.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
@@ -190,6 +230,13 @@ def cosenu_set_state(h, host):
 
 def cosenu_set_state_device(h, dev_ptr, n):
     return _check(h, load().cosenu_set_state_device(h, ctypes.c_void_p(int(dev_ptr)), int(n)))
+
+
+def cosenu_set_state_collective(h, alpha=0.9, sigma_nu=0.6, sigma_nubar=0.5, eps0=1e-6,
+                                seed=12866):
+    return _check(h, load().cosenu_set_state_collective(h, float(alpha), float(sigma_nu),
+                                                         float(sigma_nubar), float(eps0),
+                                                         int(seed)))
 
 
 def cosenu_get_state(h, out):
@@ -359,6 +406,91 @@ def cosenu_batch_last_error(b=None):
     return load().cosenu_batch_last_error(b).decode()
 
 
+# ---------------------------------------------------------------- serving
+
+def _scheck(srv, rc):
+    if rc < 0:
+        raise CosenuError(rc, load().cosenu_server_last_error(srv).decode())
+    return rc
+
+
+def cosenu_server_create(budget_bytes, max_running=0, round_steps=0):
+    lib = load()
+    srv = lib.cosenu_server_create(int(budget_bytes), int(max_running), int(round_steps))
+    if not srv:
+        raise CosenuError(COSENU_EINVAL, lib.cosenu_server_last_error(None).decode())
+    return srv
+
+
+def cosenu_server_destroy(srv):
+    load().cosenu_server_destroy(srv)
+
+
+def cosenu_submit(srv, req):
+    t = ctypes.c_uint64(0)
+    _scheck(srv, load().cosenu_submit(srv, ctypes.byref(req), ctypes.byref(t)))
+    return int(t.value)
+
+
+def _result(r):
+    c = r.conserved
+    return {"status": r.status, "steps": r.steps, "t_submit": r.t_submit, "t_admit": r.t_admit,
+            "t_done": r.t_done,
+            "conserved": {"tr_nu": c.tr_nu, "tr_nubar": c.tr_nubar, "M": np.array(c.M[:]),
+                          "M_vac": c.M_vac, "dP_max": c.dP_max, "dP_mean": c.dP_mean}}
+
+
+def cosenu_poll(srv, ticket):
+    """(rc, result dict): rc COSENU_PENDING while the run is unfinished, 0 once done."""
+    r = cosenu_result()
+    rc = _scheck(srv, load().cosenu_poll(srv, int(ticket), ctypes.byref(r)))
+    return rc, _result(r)
+
+
+def cosenu_wait(srv, ticket, timeout_s=-1.0):
+    r = cosenu_result()
+    rc = _scheck(srv, load().cosenu_wait(srv, int(ticket), float(timeout_s), ctypes.byref(r)))
+    return rc, _result(r)
+
+
+def cosenu_cancel(srv, ticket):
+    return _scheck(srv, load().cosenu_cancel(srv, int(ticket)))
+
+
+def cosenu_server_get_stats(srv):
+    st = cosenu_server_stats()
+    _scheck(srv, load().cosenu_server_get_stats(srv, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in cosenu_server_stats._fields_}
+
+
+def cosenu_server_last_error(srv=None):
+    return load().cosenu_server_last_error(srv).decode()
+
+
+def make_request(nz, nv, L, scheme=COSENU_FDKO, precision=COSENU_MIXED, nsteps=1, state=None,
+                 out_state=None, alpha=0.9, sigma_nu=0.6, sigma_nubar=0.5, eps0=1e-6, seed=12866,
+                 **params):
+    """A cosenu_request.  `state` / `out_state`: C-contiguous float64 numpy arrays (kept
+    referenced by the returned object) or None.  Parameters not given take the library
+    defaults (dt: 0.4 dz)."""
+    p = cosenu_params(mu=1.0, omega=0.0, theta=0.0, lambda_=0.0, ko_eps=0.1, weno_eps=1e-6,
+                      dt=0.0)
+    for k, v in params.items():
+        setattr(p, "lambda_" if k in ("lambda", "lam") else k, float(v))
+    r = cosenu_request(nz=int(nz), nv=int(nv), L=float(L), scheme=int(scheme),
+                       precision=int(precision), params=p, nsteps=int(nsteps),
+                       state=None, alpha=float(alpha), sigma_nu=float(sigma_nu),
+                       sigma_nubar=float(sigma_nubar), eps0=float(eps0), seed=int(seed),
+                       out_state=None)
+    for name, arr in (("state", state), ("out_state", out_state)):
+        if arr is not None:
+            assert arr.dtype == np.float64 and arr.flags["C_CONTIGUOUS"]
+            assert arr.size == 8 * int(nz) * int(nv)
+            setattr(r, name, _dptr(arr))
+    r._keep = (state, out_state)
+    return r
+
+
 # ---------------------------------------------------------------- owner objects
 
 class Solver:
@@ -487,3 +619,52 @@ class Batch:
 
     def device_bytes(self):
         return cosenu_batch_device_bytes(self.b)
+
+
+class Server:
+    """Owns one serving loop: Server(budget_bytes, max_running=0, round_steps=0)."""
+
+    def __init__(self, budget_bytes, max_running=0, round_steps=0):
+        self.s = cosenu_server_create(budget_bytes, max_running, round_steps)
+        self._reqs = {}
+
+    def close(self):
+        if self.s:
+            cosenu_server_destroy(self.s)
+            self.s = None
+            self._reqs.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def submit(self, req):
+        t = cosenu_submit(self.s, req)
+        self._reqs[t] = req  # keeps the request's buffers alive until collected
+        return t
+
+    def poll(self, ticket):
+        rc, res = cosenu_poll(self.s, ticket)
+        if rc == COSENU_OK:
+            self._reqs.pop(ticket, None)
+        return rc, res
+
+    def wait(self, ticket, timeout_s=-1.0):
+        rc, res = cosenu_wait(self.s, ticket, timeout_s)
+        if rc == COSENU_OK:
+            self._reqs.pop(ticket, None)
+        return rc, res
+
+    def cancel(self, ticket):
+        cosenu_cancel(self.s, ticket)
+
+    def stats(self):
+        return cosenu_server_get_stats(self.s)

@@ -574,6 +574,57 @@ int cosenu_set_state_device(cosenu_t h, const double* dev, size_t n) {
   return COSENU_OK;
 }
 
+int cosenu_set_state_collective(cosenu_t h, double alpha, double sigma_nu, double sigma_nubar,
+                                double eps0, uint64_t seed) {
+  if (!h) return fail(h, COSENU_EINVAL, "NULL handle");
+  if (!std::isfinite(alpha) || !std::isfinite(eps0) || !(sigma_nu > 0.0) ||
+      !(sigma_nubar > 0.0) || !std::isfinite(sigma_nu) || !std::isfinite(sigma_nubar))
+    return fail(h, COSENU_EINVAL, "need finite alpha, eps0 and positive finite sigmas");
+  const int64_t nz = h->nz;
+  const int nv = h->nv;
+  // the two species' angular factors g_nu(v) and alpha g_nubar(v), normalised on the bins
+  std::vector<double> hv((size_t)2 * nv + (size_t)2 * nz);
+  const double dv = 2.0 / nv;
+  for (int s = 0; s < 2; ++s) {
+    const double sig = s == 0 ? sigma_nu : sigma_nubar;
+    double sum = 0.0;
+    for (int j = 0; j < nv; ++j) {
+      const double v = -1.0 + (j + 0.5) * dv;
+      hv[(size_t)s * nv + j] = std::exp(-((v - 1.0) * (v - 1.0)) / (2.0 * sig * sig));
+      sum += hv[(size_t)s * nv + j];
+    }
+    const double norm = sum * dv;
+    for (int j = 0; j < nv; ++j)
+      hv[(size_t)s * nv + j] = (s == 0 ? 1.0 : alpha) * (hv[(size_t)s * nv + j] / norm);
+  }
+  // off-diagonal seed eps0 exp(i phi(z)), phi = 2 pi u, u = (splitmix64(z ^ seed) >> 11) 2^-53
+  double* ph = hv.data() + (size_t)2 * nv;
+  for (int64_t z = 0; z < nz; ++z) {
+    uint64_t x = ((uint64_t)z ^ seed) + 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    x ^= x >> 31;
+    const double phi = 2.0 * M_PI * ((double)(x >> 11) * 0x1.0p-53);
+    ph[z] = eps0 * std::cos(phi);
+    ph[nz + z] = eps0 * std::sin(phi);
+  }
+  // the factors go through the delta_1 buffer (free between steps; 32 nz nv >= 16 (nz + nv) bytes)
+  double* dev = static_cast<double*>(h->d[0]);
+  h->ycur = 0;
+  CK(h, cudaMemcpyAsync(dev, hv.data(), hv.size() * sizeof(double), cudaMemcpyHostToDevice,
+                        h->stream));
+  const int64_t n = 8 * nz * (int64_t)nv;
+  collective_fill_kernel<<<(int)std::min<int64_t>((n + 255) / 256, 8192), 256, 0, h->stream>>>(
+      h->y[0], nz, nv, dev, dev + 2 * nv);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  CK(h, cudaGetLastError());
+  CK(h, refresh_moments(h));
+  CK(h, cudaMemsetAsync(h->err, 0, 64, h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));  // hv dies here
+  h->steps = 0;
+  return COSENU_OK;
+}
+
 int cosenu_get_state(cosenu_t h, double* host, size_t n) {
   if (!h || !host) return fail(h, COSENU_EINVAL, "NULL argument");
   if (int rc = check_n(h, n)) return rc;

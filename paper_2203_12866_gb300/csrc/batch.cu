@@ -574,9 +574,12 @@ int cosenu_batch_step(cosenu_batch_t b, int64_t nsteps) {
   return run_steps(b, nsteps, true);
 }
 
-int cosenu_batch_sync(cosenu_batch_t b, int32_t* first_bad) {
-  if (!b) return bfail(b, COSENU_EINVAL, "NULL batch");
-  if (first_bad) *first_bad = -1;
+}  // extern "C"
+
+namespace cosenu {
+
+int batch_member_flags(cosenu_batch_t b, std::vector<uint32_t>* flags) {
+  flags->clear();
   if (int rc = plan(b)) return rc;
   const int n = (int)b->members.size();
   if (n == 0) return COSENU_OK;
@@ -588,10 +591,23 @@ int cosenu_batch_sync(cosenu_batch_t b, int32_t* first_bad) {
   BCK(b, cudaMemcpyAsync(b->flags_host, out, n * sizeof(uint32_t), cudaMemcpyDeviceToHost,
                          b->stream));
   BCK(b, cudaStreamSynchronize(b->stream));
+  flags->assign(b->flags_host, b->flags_host + n);
+  return COSENU_OK;
+}
+
+}  // namespace cosenu
+
+extern "C" {
+
+int cosenu_batch_sync(cosenu_batch_t b, int32_t* first_bad) {
+  if (!b) return bfail(b, COSENU_EINVAL, "NULL batch");
+  if (first_bad) *first_bad = -1;
+  std::vector<uint32_t> flags;
+  if (int rc = batch_member_flags(b, &flags)) return rc;
   uint32_t any = 0;
-  for (int i = 0; i < n; ++i) {
-    if (b->flags_host[i] && first_bad && *first_bad < 0) *first_bad = i;
-    any |= b->flags_host[i];
+  for (size_t i = 0; i < flags.size(); ++i) {
+    if (flags[i] && first_bad && *first_bad < 0) *first_bad = (int32_t)i;
+    any |= flags[i];
   }
   if (any & kErrTimeout) return bfail(b, COSENU_ETIMEOUT, "a device-side wait gave up");
   if (any) return bfail(b, COSENU_ENONFINITE, "non-finite value in a member's state");

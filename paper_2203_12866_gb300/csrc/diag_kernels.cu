@@ -114,6 +114,23 @@ __global__ void __launch_bounds__(256) apply_increment_batch_kernel(
   }
 }
 
+// Collective-run initial state from its factors: y[s][0][z][v] = g[s][v],
+// y[s][1][z][v] = 0, y[s][2][z][v] = ph[0][z], y[s][3][z][v] = ph[1][z].
+__global__ void collective_fill_kernel(double* __restrict__ y, int64_t nz, int nv,
+                                       const double* __restrict__ g,
+                                       const double* __restrict__ ph) {
+  const int64_t plane = nz * nv;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < 8 * plane;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int q = (int)(e / plane);
+    const int64_t r = e - (int64_t)q * plane;
+    const int64_t z = r / nv;
+    const int v = (int)(r - z * nv);
+    const int c = q & 3, s = q >> 2;
+    y[e] = c == 0 ? g[s * nv + v] : c == 1 ? 0.0 : ph[(int64_t)(c - 2) * nz + z];
+  }
+}
+
 // out[k] = *flags[k] (the error words of n handles); clears them if `clear`.
 __global__ void gather_flags_kernel(uint32_t* const* __restrict__ flags, int n,
                                     uint32_t* __restrict__ out, int clear) {

@@ -28,6 +28,9 @@ __global__ void apply_increment_kernel(double* __restrict__ y, float* __restrict
 __global__ void apply_increment_batch_kernel(const ApplySeg* __restrict__ segs,
                                              const int64_t* __restrict__ chunk_first, int nseg,
                                              int64_t nchunks);
+__global__ void collective_fill_kernel(double* __restrict__ y, int64_t nz, int nv,
+                                       const double* __restrict__ g,
+                                       const double* __restrict__ ph);
 __global__ void gather_flags_kernel(uint32_t* const* __restrict__ flags, int n,
                                     uint32_t* __restrict__ out, int clear);
 __global__ void zavg_kernel(const double* __restrict__ y, int64_t nz, int nv,

@@ -101,6 +101,10 @@ void destroy_member(cosenu_t h);
 // (launch-shape fields from h->cfg).
 StageArgs stage_args(const cosenu_s* h, int stage, int ycur);
 
+// Wait for the batch's stream; (*flags)[i] = error bits of member i (then
+// cleared on the device).
+int batch_member_flags(cosenu_batch_t b, std::vector<uint32_t>* flags);
+
 // The state buffer that follows a step from `ycur` (the mixed path updates in place).
 inline int next_y(const cosenu_s* h, int ycur) {
   return h->precision == COSENU_FP64 ? ycur ^ 1 : ycur;

@@ -151,3 +151,24 @@ def batch_instances(n: int, *, seed=12866, nz_range=(1024, 32768), nv_choices=(3
                     "sigma_nubar": float(s_nb), "scheme": scheme, "L": nz * dz, "dt": cfl * dz,
                     "seed": seed + 1000 + i})
     return out
+
+
+def serving_trace(n: int, rate: float, *, seed=12866, step_scale=1.0, **grid_kw):
+    """A trace of n runs for the serving loop: arrival times of a Poisson process
+    of `rate` runs per second (exponential gaps -ln(1 - u) / rate from uniform01
+    stream seed + 100), grids from batch_instances(n, seed=seed, **grid_kw),
+    precision alternating mixed / FP64 (run i: mixed if i is even), and a final
+    time t_final = U[50, 500] / mu (stream seed + 101) turned into
+    nsteps = max(1, round(step_scale * t_final / dt)).  Returns a list of dicts
+    (the batch_instances fields plus t_arrival, precision, nsteps)."""
+    runs = batch_instances(n, seed=seed, **grid_kw)
+    gaps = -np.log1p(-uniform01(n, seed + 100)) / rate
+    tf = uniform01(n, seed + 101)
+    t = 0.0
+    for i, r in enumerate(runs):
+        t += float(gaps[i])
+        r["t_arrival"] = t
+        r["precision"] = 1 if i % 2 == 0 else 0
+        t_final = (50.0 + 450.0 * float(tf[i])) / r["mu"]
+        r["nsteps"] = max(1, int(round(step_scale * t_final / r["dt"])))
+    return runs
