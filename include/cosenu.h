@@ -47,8 +47,11 @@ extern "C" {
 
 #define COSENU_VERSION 1
 
-/* Spatial scheme: Sec. 3.1 (FD4 + Kreiss-Oliger r = 2) or Sec. 3.2 (FV WENO7). */
-enum { COSENU_FDKO = 0, COSENU_WENO7 = 1 };
+/* Spatial scheme: Sec. 3.1 (FD4 + Kreiss-Oliger r = 2), Sec. 3.2 (FV WENO7), or
+ * FD4 + Kreiss-Oliger r = 3 (the general dissipation operator of Sec. 3.1 at
+ * r = 3: right-hand side +(eps_ko / (64 dz)) (u_{-3} - 6u_{-2} + 15u_{-1}
+ * - 20u_0 + 15u_{+1} - 6u_{+2} + u_{+3}); 3 halo rows). */
+enum { COSENU_FDKO = 0, COSENU_WENO7 = 1, COSENU_FDKO3 = 2 };
 
 /* Arithmetic.  COSENU_FP64: every operation in double.  COSENU_MIXED: the
  * state y and its RK4 update y += increment stay in double, the per-z

@@ -27,7 +27,7 @@ _HDR = os.path.join(_HERE, "cosenu_oracle.h")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "libcosenu_oracle.so")
 
-FDKO, WENO7 = 0, 1
+FDKO, WENO7, FDKO3 = 0, 1, 2
 _lock = threading.Lock()
 _default = None
 
@@ -89,7 +89,7 @@ def params(nz, nv, L, scheme=FDKO, *, mu=1.0, omega=0.0, theta=0.0, lam=0.0, ko_
 class OracleLib:
     """The oracle's entry points on numpy arrays, bound to one compiled library."""
 
-    FDKO, WENO7 = FDKO, WENO7
+    FDKO, WENO7, FDKO3 = FDKO, WENO7, FDKO3
     params = staticmethod(params)
 
     def __init__(self, path: str):

@@ -56,7 +56,7 @@ void oracle_vgrid(int32_t nv, double* v, double* w) {
 
 static int check(const oracle_params* p) {
   if (!p || p->nz < 1 || p->nv < 1 || !(p->L > 0.0)) return -1;
-  if (p->scheme != 0 && p->scheme != 1) return -1;
+  if (p->scheme < 0 || p->scheme > 2) return -1;
   if (p->hmode != 0 && p->hmode != 1) return -1;
   return 0;
 }
@@ -245,7 +245,7 @@ int oracle_rhs(const oracle_params* p, const double* u, double* k) {
 
         for (int c = 0; c < 4; ++c) {
           double adv;
-          if (p->scheme == 0) {
+          if (p->scheme == 0 || p->scheme == 2) {
             /* Sec. 3.1: 4th-order central difference for d/dz */
             const double um2 = u[idx(p, s, c, wrap(z - 2, nz), j)];
             const double um1 = u[idx(p, s, c, wrap(z - 1, nz), j)];
@@ -253,13 +253,26 @@ int oracle_rhs(const oracle_params* p, const double* u, double* k) {
             const double up1 = u[idx(p, s, c, wrap(z + 1, nz), j)];
             const double up2 = u[idx(p, s, c, wrap(z + 2, nz), j)];
             const double dudz = (um2 - 8.0 * um1 + 8.0 * up1 - up2) / (12.0 * h);
-            /* Kreiss-Oliger, r = 2: Q = eps (-1)^r h^(2r-1) (D+)^r (D-)^r / 2^(2r);
-             * D+D- u_i = (u_{i+1} - 2u_i + u_{i-1}) / h^2 applied twice. */
-            const double dd_m1 = (u0 - 2.0 * um1 + um2) / (h * h);
-            const double dd_0 = (up1 - 2.0 * u0 + um1) / (h * h);
-            const double dd_p1 = (up2 - 2.0 * up1 + u0) / (h * h);
-            const double dddd = (dd_p1 - 2.0 * dd_0 + dd_m1) / (h * h);
-            const double Qu = p->ko_eps * 1.0 /* (-1)^2 */ * (h * h * h) * dddd / 16.0;
+            double Qu;
+            if (p->scheme == 0) {
+              /* Kreiss-Oliger, r = 2: Q = eps (-1)^r h^(2r-1) (D+)^r (D-)^r / 2^(2r);
+               * D+D- u_i = (u_{i+1} - 2u_i + u_{i-1}) / h^2 applied twice. */
+              const double dd_m1 = (u0 - 2.0 * um1 + um2) / (h * h);
+              const double dd_0 = (up1 - 2.0 * u0 + um1) / (h * h);
+              const double dd_p1 = (up2 - 2.0 * up1 + u0) / (h * h);
+              const double dddd = (dd_p1 - 2.0 * dd_0 + dd_m1) / (h * h);
+              Qu = p->ko_eps * 1.0 /* (-1)^2 */ * (h * h * h) * dddd / 16.0;
+            } else {
+              /* Kreiss-Oliger, r = 3 (the general form of Sec. 3.1 with r = 3):
+               * Q = eps (-1)^3 h^5 (D+)^3 (D-)^3 / 2^6; D+D- applied three times
+               * to u_{z-3..z+3}, each pass shortening the row by one on each side. */
+              double dd[7];
+              for (int m = -3; m <= 3; ++m) dd[m + 3] = u[idx(p, s, c, wrap(z + m, nz), j)];
+              for (int pass = 0, len = 7; pass < 3; ++pass, len -= 2)
+                for (int i = 0; i + 2 < len; ++i)
+                  dd[i] = (dd[i + 2] - 2.0 * dd[i + 1] + dd[i]) / (h * h);
+              Qu = p->ko_eps * -1.0 /* (-1)^3 */ * (h * h * h * h * h) * dd[0] / 64.0;
+            }
             /* d_t u + Q u = ... (reading R4) */
             adv = -vg[j] * dudz - Qu;
           } else {

@@ -14,8 +14,8 @@
  *     Hbar = H_vac - mu int dv' (1 - v v') [rho*(v') - alpha rhobar(v')]:
  *     Sec. 2, Eq. (ham) with the printed H_vac;
  *   - v grid: N_v bins on [-1,1], beam at bin midpoint, Riemann sum: Sec. 3;
- *   - FD: 4th-order central difference + Kreiss-Oliger dissipation (r = 2),
- *     method of lines: Sec. 3.1;
+ *   - FD: 4th-order central difference + Kreiss-Oliger dissipation (r = 2,
+ *     or r = 3 from the general form of Q), method of lines: Sec. 3.1;
  *   - FV: cell-average update Eq. (cell_av) with 7th-order WENO flux,
  *     Eqs. (fn_w_lin_comb), (weight), Appendix A Eqs. (f7), (f4s), (Si4),
  *     Algorithm 1;
@@ -37,7 +37,9 @@
  *   R4 Kreiss-Oliger: the paper adds Q u to the time-derivative side
  *      (d_t u -> d_t u + Q u), so the right-hand side receives -Q u; for
  *      r = 2 that is -(eps_ko / (16 dz)) (u_{-2} - 4u_{-1} + 6u_0 - 4u_{+1} + u_{+2}),
- *      which is dissipative.  h = dz.
+ *      which is dissipative; for r = 3 it is
+ *      +(eps_ko / (64 dz)) (u_{-3} - 6u_{-2} + 15u_{-1} - 20u_0 + 15u_{+1} - 6u_{+2} + u_{+3}),
+ *      also dissipative.  h = dz.
  *   R5 alpha is absorbed into the stored antineutrino state (Sbar = alpha g rhobar),
  *      so the code's Hamiltonian uses Sbar where Eq. (ham) has alpha rhobar.
  *   R6 an optional constant matter potential lambda enters as diag(lambda,0)
@@ -63,7 +65,7 @@ typedef struct {
   int64_t nz;        /* z cells, periodic, z in [-L/2, L/2) */
   int32_t nv;        /* v bins on [-1, 1] */
   double L;          /* domain length */
-  int32_t scheme;    /* 0 = FD4 + Kreiss-Oliger, 1 = FV WENO7 */
+  int32_t scheme;    /* 0 = FD4 + Kreiss-Oliger r = 2, 1 = FV WENO7, 2 = FD4 + Kreiss-Oliger r = 3 */
   int32_t hmode;     /* 0 = O(Nv) quadrature per beam (Eq. ham as written), 1 = separable moments */
   double mu, omega, theta, lambda;
   double ko_eps;     /* Kreiss-Oliger strength (0.1 in the paper) */

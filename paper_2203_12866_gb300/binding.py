@@ -15,7 +15,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libcosenu.so")
 
-COSENU_FDKO, COSENU_WENO7 = 0, 1
+COSENU_FDKO, COSENU_WENO7, COSENU_FDKO3 = 0, 1, 2
 COSENU_FP64, COSENU_MIXED = 0, 1
 COSENU_OK, COSENU_EINVAL, COSENU_ENOMEM, COSENU_ECUDA, COSENU_ENONFINITE, COSENU_ETIMEOUT = (
     0, -1, -2, -3, -4, -5)

@@ -34,7 +34,7 @@ size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
 bool valid_sizes(int64_t nz, int32_t nv, int scheme, int precision) {
   return nz >= 1 && nv >= 4 && nv <= 256 && nv % 4 == 0 &&
-         (scheme == COSENU_FDKO || scheme == COSENU_WENO7) &&
+         (scheme == COSENU_FDKO || scheme == COSENU_WENO7 || scheme == COSENU_FDKO3) &&
          (precision == COSENU_FP64 || precision == COSENU_MIXED) &&
          nz <= ((int64_t)1 << 40) / ((int64_t)8 * nv);
 }
@@ -159,6 +159,9 @@ StageTraits stage_traits(int scheme, int precision, int stage) {
   if (scheme == COSENU_FDKO)
     return precision == COSENU_FP64 ? traits_for_stage<kFDKO, kFP64>(stage)
                                     : traits_for_stage<kFDKO, kMIXED>(stage);
+  if (scheme == COSENU_FDKO3)
+    return precision == COSENU_FP64 ? traits_for_stage<kFDKO3, kFP64>(stage)
+                                    : traits_for_stage<kFDKO3, kMIXED>(stage);
   return precision == COSENU_FP64 ? traits_for_stage<kWENO7, kFP64>(stage)
                                   : traits_for_stage<kWENO7, kMIXED>(stage);
 }
@@ -168,6 +171,10 @@ int max_blocks(int scheme, int precision, int stage, bool batched, int block, si
     return stage_max_blocks_per_sm<kFDKO, kFP64>(stage, batched, block, smem);
   if (scheme == COSENU_FDKO)
     return stage_max_blocks_per_sm<kFDKO, kMIXED>(stage, batched, block, smem);
+  if (scheme == COSENU_FDKO3)
+    return precision == COSENU_FP64
+               ? stage_max_blocks_per_sm<kFDKO3, kFP64>(stage, batched, block, smem)
+               : stage_max_blocks_per_sm<kFDKO3, kMIXED>(stage, batched, block, smem);
   if (precision == COSENU_FP64)
     return stage_max_blocks_per_sm<kWENO7, kFP64>(stage, batched, block, smem);
   return stage_max_blocks_per_sm<kWENO7, kMIXED>(stage, batched, block, smem);
@@ -247,6 +254,10 @@ cudaError_t launch_stage_kernel(int scheme, int precision, int stage, const Stag
     return launch_rk4_stage<kFDKO, kFP64>(stage, a, bt, grid, block, smem, stream);
   if (scheme == COSENU_FDKO)
     return launch_rk4_stage<kFDKO, kMIXED>(stage, a, bt, grid, block, smem, stream);
+  if (scheme == COSENU_FDKO3)
+    return precision == COSENU_FP64
+               ? launch_rk4_stage<kFDKO3, kFP64>(stage, a, bt, grid, block, smem, stream)
+               : launch_rk4_stage<kFDKO3, kMIXED>(stage, a, bt, grid, block, smem, stream);
   if (precision == COSENU_FP64)
     return launch_rk4_stage<kWENO7, kFP64>(stage, a, bt, grid, block, smem, stream);
   return launch_rk4_stage<kWENO7, kMIXED>(stage, a, bt, grid, block, smem, stream);

@@ -8,8 +8,9 @@
 
 namespace cosenu {
 
-constexpr int kFDKO = 0;
-constexpr int kWENO7 = 1;
+constexpr int kFDKO = 0;   // FD4 + Kreiss-Oliger r = 2
+constexpr int kWENO7 = 1;  // FV WENO7
+constexpr int kFDKO3 = 2;  // FD4 + Kreiss-Oliger r = 3
 constexpr int kFP64 = 0;
 constexpr int kMIXED = 1;
 

@@ -67,6 +67,14 @@ struct Scheme<kFDKO> {
   static constexpr bool kRing = true;  // unroll the march by kWin (window as a ring)
 };
 template <>
+struct Scheme<kFDKO3> {
+  static constexpr int kLag = 3;     // center = leading row - 3
+  static constexpr int kWin = 7;     // rows c-3 .. c+3 (the r = 3 dissipation)
+  static constexpr int kLo = 3;
+  static constexpr int kHi = 3;
+  static constexpr bool kRing = true;
+};
+template <>
 struct Scheme<kWENO7> {
   static constexpr int kLag = 4;     // center = leading row - 4
   static constexpr int kWin = 8;     // rows c-3 .. c+4 (face c+1/2 of either upwind side)
@@ -237,11 +245,48 @@ __device__ __forceinline__ double weno7_face(double fm3, double fm2, double fm1,
   return num / (a0 + a1 + a2 + a3);
 }
 
-// float: fast reciprocals (the mixed path's weights need no more).
+// Smoothness indicators of Eq. (Si4) as sums of squares.  SI_r is 240 times the
+// Jiang-Shu integral of the squared first three derivatives of the sub-stencil's
+// cubic; with the cubic's derivative coefficients that integral is
+//   (b1 + b3/4)^2 + (13/3) b2^2 + (781/20) b3^2,
+// which in integer differences of the four values reads
+//   SI = (20/3) D1^2 + 260 D2^2 + (781/3) D3^2
+// (D1: one-sided first difference x 6, D2: second difference, D3: third
+// difference; exact rational identity with the printed quadratic forms).  In
+// float the printed forms lose ~1e-3 (coefficients up to 1.7e4 times values of
+// order one) to cancellation, enough to turn an indicator negative and bring
+// SI + eps to zero; the squares keep every indicator >= 0 to full precision.
+__device__ __forceinline__ void weno7_si_sos(float fm3, float fm2, float fm1, float f0, float fp1,
+                                             float fp2, float fp3, float (&si)[4]) {
+  const float c1 = 20.0f / 3.0f, c2 = 260.0f, c3 = 781.0f / 3.0f;
+  const float s0a = -11.0f * f0 + 18.0f * fp1 - 9.0f * fp2 + 2.0f * fp3;
+  const float s0b = 2.0f * f0 - 5.0f * fp1 + 4.0f * fp2 - fp3;
+  const float s0c = -f0 + 3.0f * fp1 - 3.0f * fp2 + fp3;
+  const float s1a = -2.0f * fm1 - 3.0f * f0 + 6.0f * fp1 - fp2;
+  const float s12b = fm1 - 2.0f * f0 + fp1;  // shared by the two central sub-stencils
+  const float s1c = -fm1 + 3.0f * f0 - 3.0f * fp1 + fp2;
+  const float s2a = fm2 - 6.0f * fm1 + 3.0f * f0 + 2.0f * fp1;
+  const float s2c = -fm2 + 3.0f * fm1 - 3.0f * f0 + fp1;
+  const float s3a = -2.0f * fm3 + 9.0f * fm2 - 18.0f * fm1 + 11.0f * f0;
+  const float s3b = 2.0f * f0 - 5.0f * fm1 + 4.0f * fm2 - fm3;
+  const float s3c = -fm3 + 3.0f * fm2 - 3.0f * fm1 + f0;
+  si[0] = c1 * s0a * s0a + c2 * s0b * s0b + c3 * s0c * s0c;
+  si[1] = c1 * s1a * s1a + c2 * s12b * s12b + c3 * s1c * s1c;
+  si[2] = c1 * s2a * s2a + c2 * s12b * s12b + c3 * s2c * s2c;
+  si[3] = c1 * s3a * s3a + c2 * s3b * s3b + c3 * s3c * s3c;
+}
+
+// float: indicators as sums of squares, fast reciprocals (the mixed path's
+// weights need no more).
 __device__ __forceinline__ float weno7_face(float fm3, float fm2, float fm1, float f0, float fp1,
                                             float fp2, float fp3, float eps) {
+  const float c12 = 1.0f / 12.0f;
   float f4[4], si[4];
-  weno7_parts(fm3, fm2, fm1, f0, fp1, fp2, fp3, f4, si);
+  f4[0] = (3.0f * f0 + 13.0f * fp1 - 5.0f * fp2 + fp3) * c12;
+  f4[1] = (-fm1 + 7.0f * f0 + 7.0f * fp1 - fp2) * c12;
+  f4[2] = (fm2 - 5.0f * fm1 + 13.0f * f0 + 3.0f * fp1) * c12;
+  f4[3] = (-3.0f * fm3 + 13.0f * fm2 - 23.0f * fm1 + 25.0f * f0) * c12;
+  weno7_si_sos(fm3, fm2, fm1, f0, fp1, fp2, fp3, si);
   const float d[4] = {4.0f / 35.0f, 18.0f / 35.0f, 12.0f / 35.0f, 1.0f / 35.0f};
   float w[4], ws = 0.0f, num = 0.0f;
 #pragma unroll

@@ -172,3 +172,24 @@ def serving_trace(n: int, rate: float, *, seed=12866, step_scale=1.0, **grid_kw)
         t_final = (50.0 + 450.0 * float(tf[i])) / r["mu"]
         r["nsteps"] = max(1, int(round(step_scale * t_final / r["dt"])))
     return runs
+
+
+def gaussian_perturbation_state(nz: int, nv: int, L: float, *, alpha=0.9, sigma_nu=0.6,
+                                sigma_nubar=0.5, amp=1e-2, width2=50.0) -> np.ndarray:
+    """Initial state of the collective-oscillation test of Sec. 5 with the paper's
+    own perturbation (Eqs. (pert_ee), (pert_xx), (pert_ex)): at cell centres
+    z_i = -L/2 + (i + 1/2) L/nz, eps(z) = amp exp(-z^2 / width2) and
+    rho_ee = (1 + sqrt(1 - eps^2)) / 2, rho_xx = (1 - sqrt(1 - eps^2)) / 2,
+    rho_ex = eps / 2 (real), the same for rhobar; stored as S = g_nu rho and
+    Sbar = alpha g_nubar rhobar."""
+    dz = L / nz
+    z = -L / 2 + (np.arange(nz) + 0.5) * dz
+    eps = amp * np.exp(-z * z / width2)
+    root = np.sqrt(1.0 - eps * eps)
+    rho = [(1.0 + root) / 2.0, (1.0 - root) / 2.0, eps / 2.0, np.zeros(nz)]
+    g = [angular_gaussian(nv, sigma_nu), alpha * angular_gaussian(nv, sigma_nubar)]
+    s = np.empty((2, 4, nz, nv))
+    for sp in range(2):
+        for c in range(4):
+            s[sp, c] = rho[c][:, None] * g[sp][None, :]
+    return s

@@ -5,7 +5,8 @@ import numpy as np
 import oracle
 from paper_2203_12866_gb300 import binding
 
-SCHEMES = {"fdko": binding.COSENU_FDKO, "weno7": binding.COSENU_WENO7}
+SCHEMES = {"fdko": binding.COSENU_FDKO, "weno7": binding.COSENU_WENO7,
+           "fdko3": binding.COSENU_FDKO3}
 PRECS = {"fp64": binding.COSENU_FP64, "mixed": binding.COSENU_MIXED}
 
 

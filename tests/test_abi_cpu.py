@@ -45,7 +45,7 @@ def test_workspace_bytes(lib):
 
 
 @pytest.mark.parametrize("args", [(0, 32, 1.0, 0, 0), (16, 30, 1.0, 0, 0), (16, 32, -1.0, 0, 0),
-                                  (16, 32, 1.0, 2, 0), (16, 32, 1.0, 0, 7), (16, 512, 1.0, 0, 0)])
+                                  (16, 32, 1.0, 3, 0), (16, 32, 1.0, 0, 7), (16, 512, 1.0, 0, 0)])
 def test_create_rejects_bad_sizes_without_device_work(lib, args):
     with pytest.raises(binding.CosenuError) as e:
         binding.cosenu_create(*args)

@@ -10,7 +10,7 @@ from parity_util import max_abs, run_oracle
 
 pytestmark = pytest.mark.gpu
 
-FD, WENO = binding.COSENU_FDKO, binding.COSENU_WENO7
+FD, WENO, FD3 = binding.COSENU_FDKO, binding.COSENU_WENO7, binding.COSENU_FDKO3
 FP64, MIXED = binding.COSENU_FP64, binding.COSENU_MIXED
 
 
@@ -30,7 +30,8 @@ def _mix():
             (37, 8, FD, FP64), (200, 32, FD, MIXED), (513, 32, FD, MIXED),
             (64, 32, WENO, MIXED), (1031, 64, WENO, MIXED), (3, 8, FD, MIXED),
             (96, 64, FD, FP64), (250, 32, WENO, FP64), (5, 8, WENO, MIXED),
-            (777, 32, FD, MIXED), (2048, 128, FD, MIXED), (131, 128, WENO, MIXED)]):
+            (777, 32, FD, MIXED), (2048, 128, FD, MIXED), (131, 128, WENO, MIXED),
+            (300, 32, FD3, MIXED), (70, 16, FD3, FP64), (4, 8, FD3, MIXED)]):
         params = dict(mu=0.5 + 0.25 * i, omega=0.1 * (i % 3), theta=0.05 * i, ko_eps=0.1)
         params["lambda"] = 0.02 * (i % 2)
         u0 = inputs.random_state(nz, nv, seed=500 + i, offdiag=0.05)
@@ -136,7 +137,7 @@ def test_batch_params_change_rebuilds_plan():
             assert np.array_equal(m.state(), ref), i
 
 
-@pytest.mark.parametrize("scheme", [FD, WENO])
+@pytest.mark.parametrize("scheme", [FD, WENO, FD3])
 def test_batch_members_match_oracle(scheme):
     """Members of a mixed-size FP64 batch against the oracle (FP64 bound 1e-12)."""
     sizes = [(40, 16), (97, 16), (16, 8), (130, 32)]

@@ -33,6 +33,9 @@ MUTATIONS = {
     "RK4 weight of k2": ("(k1[e] + 2.0 * k2[e] + 2.0 * k3[e] + k4[e])",
                          "(k1[e] + k2[e] + 2.0 * k3[e] + k4[e])"),
     "left-endpoint velocity bins": ("v[j] = -1.0 + j * dv + 0.5 * dv;", "v[j] = -1.0 + j * dv;"),
+    "KO r = 3 normalisation 2^6": ("(h * h * h * h * h) * dd[0] / 64.0;",
+                                   "(h * h * h * h * h) * dd[0] / 32.0;"),
+    "KO r = 3 sign (-1)^3": ("Qu = p->ko_eps * -1.0 /* (-1)^3 */", "Qu = p->ko_eps * 1.0 /* (-1)^3 */"),
     "M2 sign": ("M[1] += wg[j] * h * (P[0][2] + P[1][2]);",
                 "M[1] += wg[j] * h * (P[0][2] - P[1][2]);"),
 }
@@ -45,6 +48,7 @@ PINS = [
     (pins.test_weno7_smoothness_index_is_scaled_jiang_shu, {"seed": 0}),
     (pins.test_weno7_weight_formula, {}),
     (pins.test_fdko_pure_advection_equals_dft_solution, {"ko_eps": 0.1}),
+    (pins.test_fdko3_pure_advection_equals_dft_solution, {"ko_eps": 0.1}),
     (pins.test_weno7_linear_limit_equals_dft_solution, {}),
     (pins.test_vacuum_oscillation_exact_rk4_map, {"omega": 0.5, "theta": 0.1}),
     (pins.test_hamiltonian_structure, {}),

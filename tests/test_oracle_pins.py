@@ -182,6 +182,32 @@ def test_fdko_pure_advection_equals_dft_solution(oracle, ko_eps):
     assert np.max(np.abs(got - ref)) < 1e-13
 
 
+@pytest.mark.parametrize("ko_eps", [0.1, 0.7])
+def test_fdko3_pure_advection_equals_dft_solution(oracle, ko_eps):
+    """Kreiss-Oliger with r = 3 (the general Q of Sec. 3.1 at r = 3): same exact
+    discrete solution, with the r = 3 symbol built from D+ and D-."""
+    nz, nv, L = 32, 4, 11.0
+    p = oracle.params(nz, nv, L, oracle.FDKO3, mu=0.0, ko_eps=ko_eps, cfl=0.4)
+    u0 = inputs.random_state(nz, nv, seed=15, offdiag=1.0)
+    got = oracle.step(p, u0, 25)
+    v, _ = oracle.vgrid(nv)
+    h = L / nz
+    ref = advect_dft(u0, lambda th, j: fd4_ko_symbol(th, h, v[j], ko_eps, r=3), p.dt, 25)
+    assert np.max(np.abs(got - ref)) < 1e-13
+
+
+def test_ko3_is_dissipative_and_weaker_at_long_waves():
+    """r = 3: -eps sin^6(theta/2) / h, dissipative; smaller than r = 2 for every
+    theta < pi (sin^6 <= sin^4), equal at the grid scale."""
+    theta = np.linspace(0, np.pi, 101)
+    s3 = fd4_ko_symbol(theta, 0.5, 0.0, 0.1, r=3)
+    s2 = fd4_ko_symbol(theta, 0.5, 0.0, 0.1, r=2)
+    assert np.all(s3.real <= 1e-15)
+    assert s3.real[-1] == pytest.approx(-0.1 / 0.5, rel=1e-12)
+    assert np.all(s3.real >= s2.real - 1e-15)
+    assert np.allclose(s3.real, -0.1 / 0.5 * np.sin(theta / 2) ** 6, atol=1e-15)
+
+
 def test_ko_is_dissipative(oracle):
     """The Kreiss-Oliger term removes energy at every mode (reading of Sec. 3.1)."""
     theta = np.linspace(0, np.pi, 101)
@@ -251,6 +277,9 @@ def test_convergence_orders(oracle):
     assert math.log2(e[0] / e[1]) > 5.5
     e = [gaussian_run(oracle, oracle.FDKO, n, 1.0, dt, ko_eps=0.1) for n in (80, 160)]
     assert 3.0 < math.log2(e[0] / e[1]) < 3.8
+    # r = 3 dissipation is O(h^5): the FD4 order survives
+    e = [gaussian_run(oracle, oracle.FDKO3, n, 1.0, dt, ko_eps=0.1) for n in (80, 160)]
+    assert 3.8 < math.log2(e[0] / e[1]) < 4.3
 
 
 # --------------------------------------------------------------------------- vacuum
@@ -365,7 +394,7 @@ def test_commutator_precession(oracle):
         assert np.max(np.abs(np.sum(P * dP, axis=0))) < 1e-13
 
 
-@pytest.mark.parametrize("scheme", [0, 1])
+@pytest.mark.parametrize("scheme", [0, 1, 2])
 def test_discrete_conservation_laws(oracle, scheme):
     """Periodic z: total traces of both species, the lepton-number vector
     M = sum w dz P(S - Sbar^*) (omega = 0), and its projection on B (omega != 0)

@@ -1,0 +1,156 @@
+"""Paper variants and experiments of Sec. 4-5 run through the CUDA path:
+the paper's Gaussian perturbation of the collective test (Eqs. (pert_ee),
+(pert_xx), (pert_ex)), the box-car advection test (Eq. (box)), and the role of
+Kreiss-Oliger dissipation in the FD scheme (Sec. 5: without it the FD run
+becomes unstable)."""
+import numpy as np
+import pytest
+
+from paper_2203_12866_gb300 import binding, inputs
+from parity_util import max_abs, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+FD, WENO, FD3 = binding.COSENU_FDKO, binding.COSENU_WENO7, binding.COSENU_FDKO3
+FP64, MIXED = binding.COSENU_FP64, binding.COSENU_MIXED
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built(oracle):
+    from paper_2203_12866_gb300 import build
+    build.build()
+    binding.load()
+
+
+def bloch(st):
+    a, b, cr, ci = st
+    p0 = a + b
+    return np.array([2 * cr, -2 * ci, a - b]), p0
+
+
+@pytest.mark.parametrize("scheme", [FD, WENO, FD3])
+def test_gaussian_perturbation_parity(scheme):
+    """The paper's perturbation (eps(z) = 1e-2 exp(-z^2/50)), 100 cells around
+    the bump, against the oracle (FP64 bound)."""
+    nz, nv, L = 100, 16, 60.0
+    u0 = inputs.gaussian_perturbation_state(nz, nv, L)
+    got = run_gpu(u0, L, scheme, FP64, 30, mu=1.0, dt=0.2 * L / nz)
+    ref = run_oracle(u0, L, scheme, 30, mu=1.0, dt=0.2 * L / nz)
+    assert max_abs(got, ref) <= 1e-12
+
+
+def test_flavour_waves_stay_inside_the_light_cone():
+    """Sec. 5: flavour waves never cross the light cone.  After t = 150 the
+    off-diagonal components beyond |z| = t + 40 stay at the level of the
+    initial tail (the bump's width is ~7), while inside the cone they are O(1e-2)."""
+    nz, nv, L = 2000, 100, 1200.0
+    dz = L / nz
+    u0 = inputs.gaussian_perturbation_state(nz, nv, L)
+    with binding.Solver(nz, nv, L, WENO, FP64, mu=1.0, dt=0.2 * dz) as s:
+        s.set_state(u0)
+        n = int(round(150.0 / (0.2 * dz)))
+        s.step(n)
+        s.sync()
+        st = s.state()
+    t = n * 0.2 * dz
+    z = -L / 2 + (np.arange(nz) + 0.5) * dz
+    off = np.max(np.abs(st[:, 2:]), axis=(0, 1, 3))  # per z
+    outside = np.abs(z) > t + 40.0
+    assert off[~outside].max() > 1e-3
+    assert off[outside].max() < 1e-9
+
+
+def test_kreiss_oliger_damps_the_grid_scale_mode():
+    """FD4's symbol vanishes at the grid scale (theta = pi), so a z-checkerboard
+    in the off-diagonals is not damped by advection; only the KO term removes
+    it (at rate eps/dz, Sec. 3.1).  FP64, the paper's fiducial collective
+    state with a 1e-9 checkerboard added."""
+    nz, nv, L = 2000, 100, 1200.0
+    dz = L / nz
+    base = inputs.gaussian_perturbation_state(nz, nv, L)
+    chk = 1e-9 * (-1.0) ** np.arange(nz)
+    u0 = base.copy()
+    u0[:, 2] += chk[None, :, None]
+
+    def nyquist(st):  # amplitude of the theta = pi mode of Re rho_ex, far from the bump
+        far = np.abs(-L / 2 + (np.arange(nz) + 0.5) * dz) > 300.0
+        x = st[0, 2][far] * (-1.0) ** np.arange(nz)[far][:, None]
+        return np.abs(x.mean(axis=0)).max()
+
+    amp = {}
+    for ko in (0.0, 0.1):
+        with binding.Solver(nz, nv, L, FD, FP64, mu=1.0, ko_eps=ko, dt=0.2 * dz) as s:
+            s.set_state(u0)
+            s.step(int(round(100.0 / (0.2 * dz))))
+            s.sync()
+            amp[ko] = nyquist(s.state())
+    a0 = nyquist(u0)
+    assert amp[0.0] > 0.5 * a0            # undamped without dissipation
+    assert amp[0.1] < 1e-6 * a0           # ~exp(-eps t / dz) = exp(-16.7) with KO
+
+
+def test_fd_without_ko_becomes_unstable():
+    """Sec. 5: FD without Kreiss-Oliger dissipation develops unphysical |P| / P0 > 1
+    (the paper's P3 > 1).  In the mixed precision the float rounding seeds the
+    grid-scale modes; by t = 800 the run without KO exceeds |P|/P0 = 1.5 while the
+    run with KO keeps |P|/P0 within 0.1 of 1."""
+    nz, nv, L = 2000, 100, 1200.0
+    dz = L / nz
+    u0 = inputs.gaussian_perturbation_state(nz, nv, L)
+    worst = {}
+    for ko in (0.0, 0.1):
+        with binding.Solver(nz, nv, L, FD, MIXED, mu=1.0, ko_eps=ko, dt=0.2 * dz) as s:
+            s.set_state(u0)
+            s.step(int(round(800.0 / (0.2 * dz))))
+            try:
+                s.sync()
+            except binding.CosenuError:
+                worst[ko] = np.inf
+                continue
+            P, p0 = bloch(s.state()[0])
+            worst[ko] = float(np.max(np.linalg.norm(P, axis=0) / p0))
+    assert worst[0.0] > 1.5
+    assert worst[0.1] < 1.1
+
+
+def box_state(nz, nv, L, half_width):
+    z = -L / 2 + (np.arange(nz) + 0.5) * (L / nz)
+    f = (np.abs(z) <= half_width).astype(float)
+    u = np.zeros((2, 4, nz, nv))
+    u[:, 0] = f[None, :, None]
+    u[:, 2] = 0.5 * f[None, :, None]
+    return u
+
+
+@pytest.mark.parametrize("scheme,tol", [(FD, 1e-12), (WENO, 1e-8)])
+def test_box_car_advection_parity(scheme, tol):
+    """Eq. (box) scaled to 160 cells: pure advection (mu = omega = 0) of a box,
+    GPU against the oracle.
+
+    WENO7 bound: next to a jump, the sub-stencils lying in a constant region have
+    smoothness indicators that are zero in exact arithmetic but O(1e-12) after
+    rounding (coefficients ~1e4, values ~1, unit roundoff 1e-16), i.e. 1e-6 of
+    eps = 1e-6; their weights, and hence the face values, then differ at ~1e-6
+    relative between two correct FP64 evaluations (FMA contraction, summation
+    order).  Over 100 steps with dt/dz = 0.2 that stays below 1e-8 (observed
+    1e-10); the FP64 bound 1e-12 holds for smooth data (test_parity_gpu)."""
+    nz, nv, L = 160, 8, 80.0
+    u0 = box_state(nz, nv, L, 10.0)
+    got = run_gpu(u0, L, scheme, FP64, 100, mu=0.0, dt=0.2 * L / nz)
+    ref = run_oracle(u0, L, scheme, 100, mu=0.0, dt=0.2 * L / nz)
+    assert max_abs(got, ref) <= tol
+
+
+def test_box_car_gibbs_fd_versus_weno():
+    """Sec. 4.1: across the discontinuities FD produces Gibbs oscillations, the
+    WENO7 FV scheme does not (beyond a small overshoot)."""
+    nz, nv, L = 2000, 4, 1200.0
+    u0 = box_state(nz, nv, L, 100.0)
+    dt = 0.2 * L / nz
+    n = int(round(200.0 / dt))
+    over = {}
+    for scheme in (FD, WENO):
+        st = run_gpu(u0, L, scheme, FP64, n, mu=0.0, dt=dt)
+        over[scheme] = max(st[0, 0].max() - 1.0, -st[0, 0].min())
+    assert over[FD] > 0.05
+    assert over[WENO] < 0.25 * over[FD]

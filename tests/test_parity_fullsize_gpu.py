@@ -2,8 +2,8 @@
 workload) in the launch configuration bench.py times.
 
 The oracle cannot step the whole grid, but the method is local in z: after n RK4
-steps a row depends only on rows within n * 4 * lag (lag = 2 for FD4+KO, 4 for
-WENO7; the v-moments are per row).  So for each sampled row z0 the oracle runs
+steps a row depends only on rows within n * 4 * lag (lag = 2 for FD4+KO, 3 for
+FD4+KO r = 3, 4 for WENO7; the v-moments are per row).  So for each sampled row z0 the oracle runs
 the same n steps on a periodic patch of 128 rows centred on z0, and the 33 rows
 around z0 -- farther than 2 * 4 * 4 = 32 rows from the patch edges' wrap -- must
 match the GPU's rows element by element.  Samples include both ends of the
@@ -54,9 +54,11 @@ def state_dev():
 
 
 @pytest.mark.parametrize("scheme,prec", [("fdko", "mixed"), ("fdko", "fp64"),
-                                         ("weno7", "mixed"), ("weno7", "fp64")])
+                                         ("weno7", "mixed"), ("weno7", "fp64"),
+                                         ("fdko3", "mixed")])
 def test_fullsize_sampled_rows(state_dev, scheme, prec, oracle):
-    sc = {"fdko": binding.COSENU_FDKO, "weno7": binding.COSENU_WENO7}[scheme]
+    sc = {"fdko": binding.COSENU_FDKO, "weno7": binding.COSENU_WENO7,
+          "fdko3": binding.COSENU_FDKO3}[scheme]
     pr = {"fp64": binding.COSENU_FP64, "mixed": binding.COSENU_MIXED}[prec]
     h = binding.cosenu_create(NZ, NV, L, sc, pr)
     try:

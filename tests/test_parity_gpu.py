@@ -28,7 +28,7 @@ def _built(oracle):
     binding.load()
 
 
-@pytest.mark.parametrize("scheme", ["fdko", "weno7"])
+@pytest.mark.parametrize("scheme", ["fdko", "weno7", "fdko3"])
 def test_fp64_collective_linear(scheme):
     nz, nv = 96, 32
     L = nz * (100.0 / 512)
@@ -39,7 +39,7 @@ def test_fp64_collective_linear(scheme):
     assert max_abs(got, ref) <= FP64_TOL
 
 
-@pytest.mark.parametrize("scheme", ["fdko", "weno7"])
+@pytest.mark.parametrize("scheme", ["fdko", "weno7", "fdko3"])
 def test_fp64_nonlinear_all_terms(scheme):
     """O(1) off-diagonals, vacuum term, matter term and nu-nu term all active."""
     nz, nv = 48, 16
@@ -51,7 +51,7 @@ def test_fp64_nonlinear_all_terms(scheme):
     assert max_abs(got, ref) <= FP64_TOL
 
 
-@pytest.mark.parametrize("scheme", ["fdko", "weno7"])
+@pytest.mark.parametrize("scheme", ["fdko", "weno7", "fdko3"])
 @pytest.mark.parametrize("nz,nv", [(37, 36), (53, 12), (200, 100)])
 def test_fp64_ragged_tiles(scheme, nz, nv):
     """z ranges that do not divide into the CTAs evenly, v not a multiple of 32."""
@@ -61,7 +61,7 @@ def test_fp64_ragged_tiles(scheme, nz, nv):
     assert max_abs(got, ref) <= FP64_TOL
 
 
-@pytest.mark.parametrize("scheme", ["fdko", "weno7"])
+@pytest.mark.parametrize("scheme", ["fdko", "weno7", "fdko3"])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("nz", [1, 2, 3, 5, 9])
 def test_tiny_periodic_grids(scheme, prec, nz):
@@ -76,7 +76,7 @@ def test_tiny_periodic_grids(scheme, prec, nz):
         assert max_abs(got, ref) <= 1e-5
 
 
-@pytest.mark.parametrize("scheme", ["fdko", "weno7"])
+@pytest.mark.parametrize("scheme", ["fdko", "weno7", "fdko3"])
 def test_mixed_collective_linear(scheme):
     nz, nv = 160, 64
     L = nz * (100.0 / 512)
@@ -121,7 +121,7 @@ def test_deterministic(prec):
     assert np.array_equal(a, b)
 
 
-@pytest.mark.parametrize("scheme", ["fdko", "weno7"])
+@pytest.mark.parametrize("scheme", ["fdko", "weno7", "fdko3"])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_conservation_on_gpu(scheme, prec, oracle):
     nz, nv = 128, 32
