@@ -122,6 +122,22 @@ cosenu_t cosenu_create_external(int64_t nz, int32_t nv, double L, int scheme, in
 /* Release the handle and the device memory it allocated.  NULL is a no-op. */
 void cosenu_destroy(cosenu_t h);
 
+/* Velocity quadrature of the v integral of Eq. (ham) (and of the diagnostics).
+ *   COSENU_MIDPOINT (default): nv bins of width 2/nv, beam at the bin midpoint,
+ *     Riemann sum (Sec. 3);
+ *   COSENU_TRAPEZOID: vertex points v_j = -1 + j h, h = 2/(nv - 1), trapezoid
+ *     rule (Sec. 3.1);
+ *   COSENU_SIMPSON: the same points, Simpson's rule (Sec. 3.1): the 1/3 rule on
+ *     the first nv - 4 intervals and the 3/8 rule on the last three (nv - 1 is
+ *     odd), exact for cubics.
+ * Takes effect for later steps and diagnostics; the mixed path's running
+ * moments are recomputed.  cosenu_velocities writes the nv beam velocities
+ * and weights (either pointer may be NULL).  cosenu_set_state_collective
+ * normalises g(v) with these weights. */
+enum { COSENU_MIDPOINT = 0, COSENU_TRAPEZOID = 1, COSENU_SIMPSON = 2 };
+int cosenu_set_quadrature(cosenu_t h, int32_t mode);
+int cosenu_velocities(cosenu_t h, double* v, double* w);
+
 /* Set / read the parameters.  dt <= 0 selects the default 0.4 * dz. */
 int cosenu_set_params(cosenu_t h, const cosenu_params* p);
 int cosenu_get_params(cosenu_t h, cosenu_params* p);
@@ -141,8 +157,9 @@ int cosenu_set_state_device(cosenu_t h, const double* dev, size_t n);
  * the device, and reset the step counter (waits):
  *   S_ee(z, v)    = g_nu(v),  Sbar_ee(z, v) = alpha g_nubar(v),  S_xx = Sbar_xx = 0,
  *   S_ex = Sbar_ex = eps0 exp(i phi(z)),
- * with g(v) proportional to exp(-(v - 1)^2 / (2 sigma^2)) at the bin midpoints,
- * normalised so that sum_j dv g(v_j) = 1, and the random phase
+ * with g(v) proportional to exp(-(v - 1)^2 / (2 sigma^2)) at the beam velocities,
+ * normalised so that sum_j w_j g(v_j) = 1 (quadrature weights, see
+ * cosenu_set_quadrature), and the random phase
  * phi(z_i) = 2 pi u_i, u_i = (splitmix64(i XOR seed) >> 11) 2^-53 (splitmix64:
  * x += 0x9E3779B97F4A7C15; x = (x ^ x >> 30) * 0xBF58476D1CE4E5B9;
  * x = (x ^ x >> 27) * 0x94D049BB133111EB; x ^= x >> 31).
@@ -181,6 +198,22 @@ int cosenu_moments(cosenu_t h, double* zavg, double* vmom);
 
 /* Diagnostics of the current state (waits). */
 int cosenu_conserved(cosenu_t h, cosenu_conserved_t* out);
+
+/* delta P(z, v) = |P| / P0 - 1 of every cell (Sec. 5, the error map of the
+ * collective runs), out[2 species][nz][nv] host doubles (0 where P0 <= 0),
+ * with P = (2 Re rho_ex, -2 Im rho_ex, rho_ee - rho_xx), P0 = rho_ee + rho_xx
+ * of the stored state (waits). */
+int cosenu_dp_field(cosenu_t h, double* out);
+
+/* Fourier spectrum over z (Sec. 5) of the perpendicular polarisation of one
+ * beam, x(z_i) = P1 + i P2 = 2 (Re rho_ex - i Im rho_ex) of species `species`
+ * and velocity bin `v_index`:
+ *   X(m) = sum_{i=0}^{nz-1} x(z_i) exp(-2 pi i m i / nz),  m = m0 .. m0 + nk - 1
+ * (wavenumber k = 2 pi m / L; m may be negative, taken modulo nz), written as
+ * out[2 n] = Re X(m0 + n), out[2 n + 1] = Im X(m0 + n), host doubles.  Direct
+ * transform, O(nk nz) work; 0 <= nk <= nz, nz <= 2^31 (waits). */
+int cosenu_spectrum(cosenu_t h, int32_t species, int32_t v_index, int64_t m0, int64_t nk,
+                    double* out);
 
 /* Kernel timing.  With on != 0, every kernel launch of later cosenu_step calls
  * is bracketed by CUDA events on the handle's stream (and steps are launched

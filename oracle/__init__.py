@@ -46,6 +46,7 @@ class OracleParams(ctypes.Structure):
         ("ko_eps", ctypes.c_double),
         ("weno_eps", ctypes.c_double),
         ("dt", ctypes.c_double),
+        ("vgrid", ctypes.c_int32),
     ]
 
 
@@ -76,20 +77,24 @@ def _ptr(a):
     return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
 
 
+MIDPOINT, TRAPEZOID, SIMPSON = 0, 1, 2
+
+
 def params(nz, nv, L, scheme=FDKO, *, mu=1.0, omega=0.0, theta=0.0, lam=0.0, ko_eps=0.1,
-           weno_eps=1e-6, dt=None, cfl=0.4, hmode=1) -> OracleParams:
+           weno_eps=1e-6, dt=None, cfl=0.4, hmode=1, vgrid=MIDPOINT) -> OracleParams:
     """Parameters of one run.  dt defaults to cfl * dz with max|v| taken as 1."""
     if dt is None:
         dt = cfl * L / nz
     return OracleParams(int(nz), int(nv), float(L), int(scheme), int(hmode), float(mu),
                         float(omega), float(theta), float(lam), float(ko_eps), float(weno_eps),
-                        float(dt))
+                        float(dt), int(vgrid))
 
 
 class OracleLib:
     """The oracle's entry points on numpy arrays, bound to one compiled library."""
 
     FDKO, WENO7, FDKO3 = FDKO, WENO7, FDKO3
+    MIDPOINT, TRAPEZOID, SIMPSON = 0, 1, 2
     params = staticmethod(params)
 
     def __init__(self, path: str):
@@ -98,6 +103,7 @@ class OracleLib:
         dp = P(ctypes.c_double)
         pp = P(OracleParams)
         lib.oracle_vgrid.argtypes = [ctypes.c_int32, dp, dp]
+        lib.oracle_vgrid_q.argtypes = [ctypes.c_int32, ctypes.c_int32, dp, dp]
         lib.oracle_hamiltonian.argtypes = [pp, dp, dp]
         lib.oracle_rhs.argtypes = [pp, dp, dp]
         lib.oracle_step.argtypes = [pp, dp, ctypes.c_int64]
@@ -114,10 +120,13 @@ class OracleLib:
         assert u.size == 8 * p.nz * p.nv, "state must be [2][4][nz][nv]"
         return u
 
-    def vgrid(self, nv):
+    def vgrid(self, nv, mode=MIDPOINT):
         v = np.empty(nv)
         w = np.empty(nv)
-        self.lib.oracle_vgrid(nv, _ptr(v), _ptr(w))
+        if mode == MIDPOINT:
+            self.lib.oracle_vgrid(nv, _ptr(v), _ptr(w))
+        else:
+            assert self.lib.oracle_vgrid_q(nv, int(mode), _ptr(v), _ptr(w)) == 0
         return v, w
 
     def hamiltonian(self, p, u):
@@ -175,8 +184,8 @@ def _lib() -> OracleLib:
     return _default
 
 
-def vgrid(nv):
-    return _lib().vgrid(nv)
+def vgrid(nv, mode=MIDPOINT):
+    return _lib().vgrid(nv, mode)
 
 
 def hamiltonian(p, u):

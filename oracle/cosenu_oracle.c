@@ -54,10 +54,50 @@ void oracle_vgrid(int32_t nv, double* v, double* w) {
   }
 }
 
+/* Sec. 3.1: vertex-centred points on [-1, 1], v_j = -1 + j h, integrals by the
+ * trapezoid rule (mode 1) or Simpson's rule (mode 2).  The weights are built
+ * panel by panel: trapezoid panels [j, j+1] add h/2 to both ends; Simpson
+ * panels [k, k+2] add h/3 (1, 4, 1); an odd interval count ends with one 3/8
+ * panel [n-3, n] adding 3h/8 (1, 3, 3, 1). */
+int oracle_vgrid_q(int32_t nv, int32_t mode, double* v, double* w) {
+  if (mode == 0) {
+    oracle_vgrid(nv, v, w);
+    return 0;
+  }
+  if ((mode == 1 && nv < 2) || (mode == 2 && nv < 3) || (mode != 1 && mode != 2)) return -1;
+  const int32_t n = nv - 1; /* intervals */
+  const double h = 2.0 / n;
+  for (int32_t j = 0; j < nv; ++j) {
+    v[j] = -1.0 + j * h;
+    w[j] = 0.0;
+  }
+  if (mode == 1) {
+    for (int32_t j = 0; j < n; ++j) {
+      w[j] += h / 2.0;
+      w[j + 1] += h / 2.0;
+    }
+    return 0;
+  }
+  const int32_t n13 = (n % 2 == 0) ? n : n - 3; /* intervals covered by the 1/3 rule */
+  for (int32_t k = 0; k + 2 <= n13; k += 2) {
+    w[k] += h / 3.0;
+    w[k + 1] += 4.0 * h / 3.0;
+    w[k + 2] += h / 3.0;
+  }
+  if (n13 < n) {
+    w[n - 3] += 3.0 * h / 8.0;
+    w[n - 2] += 9.0 * h / 8.0;
+    w[n - 1] += 9.0 * h / 8.0;
+    w[n] += 3.0 * h / 8.0;
+  }
+  return 0;
+}
+
 static int check(const oracle_params* p) {
   if (!p || p->nz < 1 || p->nv < 1 || !(p->L > 0.0)) return -1;
   if (p->scheme < 0 || p->scheme > 2) return -1;
   if (p->hmode != 0 && p->hmode != 1) return -1;
+  if (p->vgrid < 0 || p->vgrid > 2 || (p->vgrid > 0 && p->nv < 3)) return -1;
   return 0;
 }
 
@@ -137,7 +177,7 @@ int oracle_hamiltonian(const oracle_params* p, const double* u, double* out) {
   const int32_t nv = p->nv;
   double* vg = (double*)malloc(sizeof(double) * nv);
   double* wg = (double*)malloc(sizeof(double) * nv);
-  oracle_vgrid(nv, vg, wg);
+  oracle_vgrid_q(nv, p->vgrid, vg, wg);
 #pragma omp parallel for schedule(static)
   for (int64_t z = 0; z < p->nz; ++z) {
     cplx* hm = (cplx*)malloc(sizeof(cplx) * 2 * nv * 4);
@@ -217,7 +257,7 @@ int oracle_rhs(const oracle_params* p, const double* u, double* k) {
   const double h = p->L / (double)nz;
   double* vg = (double*)malloc(sizeof(double) * nv);
   double* wg = (double*)malloc(sizeof(double) * nv);
-  oracle_vgrid(nv, vg, wg);
+  oracle_vgrid_q(nv, p->vgrid, vg, wg);
 
 #pragma omp parallel for schedule(static)
   for (int64_t z = 0; z < nz; ++z) {
@@ -343,7 +383,7 @@ int oracle_conserved(const oracle_params* p, const double* u, double* out) {
   const double h = p->L / (double)nz;
   double* vg = (double*)malloc(sizeof(double) * nv);
   double* wg = (double*)malloc(sizeof(double) * nv);
-  oracle_vgrid(nv, vg, wg);
+  oracle_vgrid_q(nv, p->vgrid, vg, wg);
   double tr[2] = {0, 0}, M[3] = {0, 0, 0}, dpmax = 0.0, dpnum = 0.0, dpden = 0.0;
   for (int64_t z = 0; z < nz; ++z)
     for (int32_t j = 0; j < nv; ++j) {
@@ -392,7 +432,7 @@ int oracle_moments(const oracle_params* p, const double* u, double* zavg, double
   const int32_t nv = p->nv;
   double* vg = (double*)malloc(sizeof(double) * nv);
   double* wg = (double*)malloc(sizeof(double) * nv);
-  oracle_vgrid(nv, vg, wg);
+  oracle_vgrid_q(nv, p->vgrid, vg, wg);
   if (zavg) {
     for (int s = 0; s < 2; ++s)
       for (int c = 0; c < 4; ++c)

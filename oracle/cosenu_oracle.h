@@ -14,6 +14,7 @@
  *     Hbar = H_vac - mu int dv' (1 - v v') [rho*(v') - alpha rhobar(v')]:
  *     Sec. 2, Eq. (ham) with the printed H_vac;
  *   - v grid: N_v bins on [-1,1], beam at bin midpoint, Riemann sum: Sec. 3;
+ *     or vertex points with the trapezoid or Simpson rule: Sec. 3.1;
  *   - FD: 4th-order central difference + Kreiss-Oliger dissipation (r = 2,
  *     or r = 3 from the general form of Q), method of lines: Sec. 3.1;
  *   - FV: cell-average update Eq. (cell_av) with 7th-order WENO flux,
@@ -71,10 +72,18 @@ typedef struct {
   double ko_eps;     /* Kreiss-Oliger strength (0.1 in the paper) */
   double weno_eps;   /* epsilon of Eq. (weight) (1e-6 in the paper) */
   double dt;
+  int32_t vgrid;     /* velocity quadrature: 0 midpoint bins, 1 trapezoid, 2 Simpson (oracle_vgrid_q) */
 } oracle_params;
 
 /* v_j = -1 + (j + 1/2) dv, w_j = dv = 2 / nv. */
 void oracle_vgrid(int32_t nv, double* v, double* w);
+
+/* Velocity grid and weights of quadrature `mode`: 0 as oracle_vgrid; 1 vertex
+ * grid v_j = -1 + j h, h = 2 / (nv - 1), trapezoid rule; 2 the same grid,
+ * composite Simpson rule (the 1/3 rule on pairs of intervals; with an odd
+ * number of intervals the last three take the 3/8 rule).  Returns -1 for an
+ * unknown mode or too few points (trapezoid nv >= 2, Simpson nv >= 3). */
+int oracle_vgrid_q(int32_t nv, int32_t mode, double* v, double* w);
 
 /* Per-beam Hamiltonian, out layout [2 species][3][nz][nv]: (H_ee - H_xx, Re H_ex, Im H_ex). */
 int oracle_hamiltonian(const oracle_params* p, const double* u, double* out);

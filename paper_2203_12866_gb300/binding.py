@@ -20,21 +20,21 @@ COSENU_FP64, COSENU_MIXED = 0, 1
 COSENU_OK, COSENU_EINVAL, COSENU_ENOMEM, COSENU_ECUDA, COSENU_ENONFINITE, COSENU_ETIMEOUT = (
     0, -1, -2, -3, -4, -5)
 COSENU_ECANCELLED, COSENU_PENDING = -6, 1
+COSENU_MIDPOINT, COSENU_TRAPEZOID, COSENU_SIMPSON = 0, 1, 2
 
 # Every entry point include/cosenu.h declares.
 EXPORTS = (
     "cosenu_create", "cosenu_workspace_bytes", "cosenu_create_external", "cosenu_destroy",
-    "cosenu_set_params", "cosenu_get_params", "cosenu_set_stream", "cosenu_set_state",
-    "cosenu_set_state_device", "cosenu_set_state_collective", "cosenu_get_state", "cosenu_get_rows", "cosenu_state_device",
-    "cosenu_step",
-    "cosenu_sync", "cosenu_moments", "cosenu_conserved", "cosenu_set_stage_timing",
-    "cosenu_stage_times", "cosenu_steps_taken",
-    "cosenu_last_error", "cosenu_kernel_launches",
-    "cosenu_batch_create", "cosenu_batch_destroy", "cosenu_batch_add", "cosenu_batch_remove",
-    "cosenu_batch_size", "cosenu_batch_device_bytes", "cosenu_batch_step", "cosenu_batch_sync",
-    "cosenu_batch_member", "cosenu_batch_tune", "cosenu_batch_classes",
-    "cosenu_batch_class_info", "cosenu_batch_set_stage_timing", "cosenu_batch_stage_times",
-    "cosenu_batch_stream", "cosenu_batch_last_error",
+    "cosenu_set_quadrature", "cosenu_velocities", "cosenu_set_params", "cosenu_get_params",
+    "cosenu_set_stream", "cosenu_set_state", "cosenu_set_state_device",
+    "cosenu_set_state_collective", "cosenu_get_state", "cosenu_get_rows", "cosenu_state_device",
+    "cosenu_step", "cosenu_sync", "cosenu_moments", "cosenu_conserved", "cosenu_dp_field",
+    "cosenu_spectrum", "cosenu_set_stage_timing", "cosenu_stage_times", "cosenu_steps_taken",
+    "cosenu_last_error", "cosenu_kernel_launches", "cosenu_batch_create", "cosenu_batch_destroy",
+    "cosenu_batch_add", "cosenu_batch_remove", "cosenu_batch_size", "cosenu_batch_device_bytes",
+    "cosenu_batch_step", "cosenu_batch_sync", "cosenu_batch_member", "cosenu_batch_tune",
+    "cosenu_batch_classes", "cosenu_batch_class_info", "cosenu_batch_set_stage_timing",
+    "cosenu_batch_stage_times", "cosenu_batch_stream", "cosenu_batch_last_error",
     "cosenu_server_create", "cosenu_server_destroy", "cosenu_submit", "cosenu_poll", "cosenu_wait",
     "cosenu_cancel", "cosenu_server_get_stats", "cosenu_server_last_error",
     "cosenu_conserved_noalloc",
@@ -111,6 +111,8 @@ def load(path: str = LIB_PATH):
         "cosenu_create_external": (vp, [i64, i32, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                                         vp, sz]),
         "cosenu_destroy": (None, [vp]),
+        "cosenu_set_quadrature": (ctypes.c_int, [vp, i32]),
+        "cosenu_velocities": (ctypes.c_int, [vp, dp, dp]),
         "cosenu_set_params": (ctypes.c_int, [vp, ctypes.POINTER(cosenu_params)]),
         "cosenu_get_params": (ctypes.c_int, [vp, ctypes.POINTER(cosenu_params)]),
         "cosenu_set_stream": (ctypes.c_int, [vp, vp]),
@@ -126,6 +128,8 @@ def load(path: str = LIB_PATH):
         "cosenu_sync": (ctypes.c_int, [vp]),
         "cosenu_moments": (ctypes.c_int, [vp, dp, dp]),
         "cosenu_conserved": (ctypes.c_int, [vp, ctypes.POINTER(cosenu_conserved_t)]),
+        "cosenu_dp_field": (ctypes.c_int, [vp, dp]),
+        "cosenu_spectrum": (ctypes.c_int, [vp, i32, i32, i64, i64, dp]),
         "cosenu_set_stage_timing": (ctypes.c_int, [vp, ctypes.c_int]),
         "cosenu_stage_times": (ctypes.c_int, [vp, dp, ctypes.POINTER(i64)]),
         "cosenu_steps_taken": (i64, [vp]),
@@ -206,6 +210,17 @@ def cosenu_destroy(h):
     load().cosenu_destroy(h)
 
 
+def cosenu_set_quadrature(h, mode):
+    return _check(h, load().cosenu_set_quadrature(h, int(mode)))
+
+
+def cosenu_velocities(h, nv):
+    v = np.empty(nv)
+    w = np.empty(nv)
+    _check(h, load().cosenu_velocities(h, _dptr(v), _dptr(w)))
+    return v, w
+
+
 def cosenu_set_params(h, **kw):
     p = cosenu_get_params(h)
     for k, v in kw.items():
@@ -270,6 +285,20 @@ def cosenu_conserved(h):
     _check(h, load().cosenu_conserved(h, ctypes.byref(c)))
     return {"tr_nu": c.tr_nu, "tr_nubar": c.tr_nubar, "M": np.array(c.M[:]), "M_vac": c.M_vac,
             "dP_max": c.dP_max, "dP_mean": c.dP_mean, "step": c.step}
+
+
+def cosenu_dp_field(h, nz, nv):
+    out = np.empty((2, nz, nv))
+    _check(h, load().cosenu_dp_field(h, _dptr(out)))
+    return out
+
+
+def cosenu_spectrum(h, species, v_index, m0, nk):
+    """Complex X(m) for m = m0 .. m0 + nk - 1 (see include/cosenu.h)."""
+    out = np.empty(2 * int(nk))
+    _check(h, load().cosenu_spectrum(h, int(species), int(v_index), int(m0), int(nk),
+                                     _dptr(out)))
+    return out[0::2] + 1j * out[1::2]
 
 
 def cosenu_set_stage_timing(h, on=True):

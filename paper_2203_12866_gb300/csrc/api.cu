@@ -273,6 +273,7 @@ StageArgs stage_args(const cosenu_s* h, int stage, int ycur) {
   a.ring = h->cfg[stage].ring;
   a.rows_per_slot = h->cfg[stage].rows_per_slot;
   a.slot_bytes = h->cfg[stage].slot_bytes;
+  a.vgrid = h->vgrid;
   a.inv_dz = (double)h->nz / h->L;
   a.dt = h->p.dt;
   a.mu = h->p.mu;
@@ -455,7 +456,7 @@ cudaError_t refresh_moments(cosenu_t h) {
   y32_from_y_kernel<<<(int)std::min<int64_t>((n + 255) / 256, 8192), 256, 0, h->stream>>>(
       h->y[h->ycur], h->y32[h->ycur], n);
   ymoments_kernel<<<(int)std::min<int64_t>((h->nz + 7) / 8, 65535), 256, 0, h->stream>>>(
-      h->y[h->ycur], h->nz, h->nv, h->my, 8);
+      h->y[h->ycur], h->nz, h->nv, h->my, 8, h->vgrid);
   g_launches.fetch_add(2, std::memory_order_relaxed);
   return cudaGetLastError();
 }
@@ -545,6 +546,27 @@ int cosenu_set_params(cosenu_t h, const cosenu_params* p) {
   return COSENU_OK;
 }
 
+int cosenu_set_quadrature(cosenu_t h, int32_t mode) {
+  if (!h) return fail(h, COSENU_EINVAL, "NULL handle");
+  if (mode != COSENU_MIDPOINT && mode != COSENU_TRAPEZOID && mode != COSENU_SIMPSON)
+    return fail(h, COSENU_EINVAL, "unknown quadrature");
+  if (mode == h->vgrid) return COSENU_OK;
+  h->vgrid = mode;
+  ++h->version;
+  drop_graph(h);
+  CK(h, refresh_moments(h));  // the mixed path's running moments use the weights
+  return COSENU_OK;
+}
+
+int cosenu_velocities(cosenu_t h, double* v, double* w) {
+  if (!h) return fail(h, COSENU_EINVAL, "NULL handle");
+  for (int j = 0; j < h->nv; ++j) {
+    if (v) v[j] = vgrid_v(j, h->nv, h->vgrid);
+    if (w) w[j] = vgrid_w(j, h->nv, h->vgrid);
+  }
+  return COSENU_OK;
+}
+
 int cosenu_get_params(cosenu_t h, cosenu_params* p) {
   if (!h || !p) return fail(h, COSENU_EINVAL, "NULL argument");
   *p = h->p;
@@ -595,16 +617,20 @@ int cosenu_set_state_collective(cosenu_t h, double alpha, double sigma_nu, doubl
   const int nv = h->nv;
   // the two species' angular factors g_nu(v) and alpha g_nubar(v), normalised on the bins
   std::vector<double> hv((size_t)2 * nv + (size_t)2 * nz);
-  const double dv = 2.0 / nv;
   for (int s = 0; s < 2; ++s) {
     const double sig = s == 0 ? sigma_nu : sigma_nubar;
-    double sum = 0.0;
+    double norm = 0.0;  // sum_j w_j g(v_j)
     for (int j = 0; j < nv; ++j) {
-      const double v = -1.0 + (j + 0.5) * dv;
+      const double v = vgrid_v(j, nv, h->vgrid);
       hv[(size_t)s * nv + j] = std::exp(-((v - 1.0) * (v - 1.0)) / (2.0 * sig * sig));
-      sum += hv[(size_t)s * nv + j];
     }
-    const double norm = sum * dv;
+    if (h->vgrid == kVgridMidpoint) {  // equal weights: sum first, then scale
+      double sum = 0.0;
+      for (int j = 0; j < nv; ++j) sum += hv[(size_t)s * nv + j];
+      norm = sum * (2.0 / nv);
+    } else {
+      for (int j = 0; j < nv; ++j) norm += vgrid_w(j, nv, h->vgrid) * hv[(size_t)s * nv + j];
+    }
     for (int j = 0; j < nv; ++j)
       hv[(size_t)s * nv + j] = (s == 0 ? 1.0 : alpha) * (hv[(size_t)s * nv + j] / norm);
   }
@@ -714,12 +740,46 @@ int cosenu_moments(cosenu_t h, double* zavg, double* vmom) {
     // staged in the delta_1 buffer (free between steps), row stride 8
     double* dm = reinterpret_cast<double*>(h->d[0]);
     ymoments_kernel<<<(int)std::min<int64_t>((h->nz + 7) / 8, 65535), 256, 0, h->stream>>>(
-        y, h->nz, h->nv, dm, 8);
+        y, h->nz, h->nv, dm, 8, h->vgrid);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     CK(h, cudaGetLastError());
     CK(h, cudaMemcpy2DAsync(vmom, 6 * sizeof(double), dm, 8 * sizeof(double), 6 * sizeof(double),
                             (size_t)h->nz, cudaMemcpyDeviceToHost, h->stream));
   }
+  CK(h, cudaStreamSynchronize(h->stream));
+  return COSENU_OK;
+}
+
+int cosenu_dp_field(cosenu_t h, double* out) {
+  if (!h || !out) return fail(h, COSENU_EINVAL, "NULL argument");
+  // staged in the delta_1 buffer (free between steps; 16 nz nv <= its 32 nz nv bytes)
+  double* dev = static_cast<double*>(h->d[0]);
+  const int64_t n = 2 * h->nz * (int64_t)h->nv;
+  dp_field_kernel<<<(int)std::min<int64_t>((n + 255) / 256, 8192), 256, 0, h->stream>>>(
+      h->y[h->ycur], h->nz, h->nv, dev);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  CK(h, cudaGetLastError());
+  CK(h, cudaMemcpyAsync(out, dev, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost,
+                        h->stream));
+  CK(h, cudaStreamSynchronize(h->stream));
+  return COSENU_OK;
+}
+
+int cosenu_spectrum(cosenu_t h, int32_t species, int32_t v_index, int64_t m0, int64_t nk,
+                    double* out) {
+  if (!h || !out) return fail(h, COSENU_EINVAL, "NULL argument");
+  if (species < 0 || species > 1 || v_index < 0 || v_index >= h->nv || nk < 0 || nk > h->nz ||
+      h->nz > ((int64_t)1 << 31))
+    return fail(h, COSENU_EINVAL,
+                "need species 0 or 1, 0 <= v_index < nv, 0 <= nk <= nz, nz <= 2^31");
+  if (nk == 0) return COSENU_OK;
+  double* dev = static_cast<double*>(h->d[0]);  // 16 nk <= 16 nz bytes
+  dft_beam_kernel<<<(int)nk, 256, 0, h->stream>>>(h->y[h->ycur], h->nz, h->nv, species,
+                                                  v_index, m0, dev);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  CK(h, cudaGetLastError());
+  CK(h, cudaMemcpyAsync(out, dev, (size_t)nk * 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                        h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
   return COSENU_OK;
 }
@@ -730,7 +790,8 @@ int cosenu_conserved(cosenu_t h, cosenu_conserved_t* out) {
   const int nb = (int)std::min<int64_t>(kDiagMaxBlocks, (ncell + kDiagBlock - 1) / kDiagBlock);
   double* part = reinterpret_cast<double*>(h->ws + h->lay.partial);
   double* res = reinterpret_cast<double*>(h->ws + h->lay.result);
-  conserved_partial_kernel<<<nb, kDiagBlock, 0, h->stream>>>(h->y[h->ycur], h->nz, h->nv, part);
+  conserved_partial_kernel<<<nb, kDiagBlock, 0, h->stream>>>(h->y[h->ycur], h->nz, h->nv, part,
+                                                              h->vgrid);
   CK(h, cudaGetLastError());
   conserved_final_kernel<<<1, 32, 0, h->stream>>>(part, nb, res);
   CK(h, cudaGetLastError());

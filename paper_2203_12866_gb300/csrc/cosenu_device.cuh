@@ -39,6 +39,7 @@ struct StageArgs {
   int32_t ring;           // bulk-copy ring depth (slots)
   int32_t rows_per_slot;  // consecutive z rows per ring slot (one bulk copy per plane)
   int32_t slot_bytes;     // bytes of one ring slot
+  int32_t vgrid;          // velocity quadrature (kVgrid*)
   double inv_dz;          // 1 / dz
   double dt;
   double mu;
@@ -57,6 +58,34 @@ struct StageArgs {
   double* my;             // mixed: running FP64 moments of y, [nz][8] (6 used)
   uint32_t* err;          // device error flags
 };
+
+// ------------------------------------------------------------------ velocity grid
+// kVgridMidpoint: nv bins, beam at the bin midpoint, Riemann sum (Sec. 3).
+// kVgridTrapezoid / kVgridSimpson: vertex points v_j = -1 + j h, h = 2 / (nv - 1),
+// trapezoid or Simpson weights (Sec. 3.1).  nv is even here (a multiple of 4),
+// so nv - 1 intervals are odd: Simpson's 1/3 rule covers the first nv - 4
+// intervals and the 3/8 rule the last three.
+constexpr int kVgridMidpoint = 0;
+constexpr int kVgridTrapezoid = 1;
+constexpr int kVgridSimpson = 2;
+
+__host__ __device__ inline double vgrid_v(int j, int nv, int mode) {
+  if (mode == kVgridMidpoint) return -1.0 + (j + 0.5) * (2.0 / nv);
+  return -1.0 + j * (2.0 / (nv - 1));
+}
+
+__host__ __device__ inline double vgrid_w(int j, int nv, int mode) {
+  if (mode == kVgridMidpoint) return 2.0 / nv;
+  const int n = nv - 1;
+  const double h = 2.0 / n;
+  if (mode == kVgridTrapezoid) return (j == 0 || j == n) ? 0.5 * h : h;
+  const int m = n - 3;  // last point of the 1/3-rule part
+  if (j == n) return 3.0 * h / 8.0;
+  if (j > m) return 9.0 * h / 8.0;
+  if (j == m) return m == 0 ? 3.0 * h / 8.0 : h / 3.0 + 3.0 * h / 8.0;
+  if (j == 0) return h / 3.0;
+  return (j & 1) ? 4.0 * h / 3.0 : 2.0 * h / 3.0;
+}
 
 // ------------------------------------------------------------------ PTX
 

@@ -8,18 +8,19 @@
 
 namespace cosenu {
 
-// D_n = sum_j dv v_j^n (S_j - Sbar_j^*) of every z row, n = 0, 1 (Eq. (ham)).
-// One warp per row; lanes stride over v.  out[z * stride + k], k < 6.
+// D_n = sum_j w_j v_j^n (S_j - Sbar_j^*) of every z row, n = 0, 1 (Eq. (ham)),
+// with the beams and weights of quadrature `vgrid`.  One warp per row; lanes
+// stride over v.  out[z * stride + k], k < 6.
 __global__ void ymoments_kernel(const double* __restrict__ y, int64_t nz, int nv,
-                                double* __restrict__ out, int stride) {
+                                double* __restrict__ out, int stride, int vgrid) {
   const int lane = threadIdx.x & 31;
   const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
-  const double dv = 2.0 / nv;
   for (int64_t z = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); z < nz;
        z += warps_total) {
     double m[6] = {0, 0, 0, 0, 0, 0};
     for (int j = lane; j < nv; j += 32) {
-      const double v = -1.0 + (j + 0.5) * dv;
+      const double v = vgrid_v(j, nv, vgrid);
+      const double dv = vgrid_w(j, nv, vgrid);
       auto at = [&](int q) { return y[((int64_t)q * nz + z) * nv + j]; };
       const double d3 = (at(0) - at(1)) - (at(4) - at(5));
       const double dr = at(2) - at(6);
@@ -140,6 +141,74 @@ __global__ void gather_flags_kernel(uint32_t* const* __restrict__ flags, int n,
   }
 }
 
+// delta P(z, v) = |P| / P0 - 1 of every cell of both species (Sec. 5; 0 where
+// P0 <= 0), out[s][z][v], with P = (2 Re rho_ex, -2 Im rho_ex, rho_ee - rho_xx)
+// and P0 = rho_ee + rho_xx of the stored state.
+__global__ void dp_field_kernel(const double* __restrict__ y, int64_t nz, int nv,
+                                double* __restrict__ out) {
+  const int64_t plane = nz * nv;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < 2 * plane;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int s = e >= plane ? 1 : 0;
+    const int64_t r = e - s * plane;
+    const double a = y[(int64_t)(4 * s + 0) * plane + r];
+    const double b = y[(int64_t)(4 * s + 1) * plane + r];
+    const double cr = y[(int64_t)(4 * s + 2) * plane + r];
+    const double ci = y[(int64_t)(4 * s + 3) * plane + r];
+    const double p0 = a + b;
+    const double p1 = 2.0 * cr, p2 = -2.0 * ci, p3 = a - b;
+    out[e] = p0 > 0.0 ? sqrt(p1 * p1 + p2 * p2 + p3 * p3) / p0 - 1.0 : 0.0;
+  }
+}
+
+// Discrete Fourier transform over z of the perpendicular polarisation of beam
+// (s, j), x(z) = P1 + i P2 = 2 (Re rho_ex - i Im rho_ex):
+//   X(m) = sum_z x(z) exp(-2 pi i m z / nz),  m = m0 + blockIdx.x,
+// out[2 i], out[2 i + 1] = Re, Im X(m0 + i).  One block per m; thread t sums
+// z = t, t + blockDim, ... with the phase (m z mod nz) advanced by integer
+// additions (exact), then a fixed-order block reduction.
+__global__ void dft_beam_kernel(const double* __restrict__ y, int64_t nz, int nv, int s, int j,
+                                int64_t m0, double* __restrict__ out) {
+  __shared__ double red[2][32];
+  const int64_t plane = nz * nv;
+  const int64_t m = ((m0 + (int64_t)blockIdx.x) % nz + nz) % nz;
+  const int64_t step = (m * (int64_t)blockDim.x) % nz;
+  int64_t ph = (m * (int64_t)threadIdx.x) % nz;
+  const double* cr = y + (int64_t)(4 * s + 2) * plane + j;
+  const double* ci = y + (int64_t)(4 * s + 3) * plane + j;
+  const double inv = 2.0 / (double)nz;
+  double re = 0.0, im = 0.0;
+  for (int64_t z = threadIdx.x; z < nz; z += blockDim.x) {
+    double sn, cs;
+    sincospi(inv * (double)ph, &sn, &cs);  // theta = 2 pi ph / nz
+    const double xr = 2.0 * cr[z * nv], xi = -2.0 * ci[z * nv];
+    re += xr * cs + xi * sn;
+    im += xi * cs - xr * sn;
+    ph += step;
+    if (ph >= nz) ph -= nz;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    re += __shfl_xor_sync(0xffffffffu, re, o);
+    im += __shfl_xor_sync(0xffffffffu, im, o);
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    red[0][w] = re;
+    red[1][w] = im;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      a += red[0][k];
+      b += red[1][k];
+    }
+    out[2 * (int64_t)blockIdx.x] = a;
+    out[2 * (int64_t)blockIdx.x + 1] = b;
+  }
+}
+
 // Column sums over z: out[q][v] = (1/nz) sum_z y[q][z][v].  Block = (q, 32 v);
 // 8 warps split z, partial sums combined in a fixed order.
 __global__ void zavg_kernel(const double* __restrict__ y, int64_t nz, int nv,
@@ -160,17 +229,20 @@ __global__ void zavg_kernel(const double* __restrict__ y, int64_t nz, int nv,
   }
 }
 
-// Per-block partial sums of the diagnostics over (z, v) cells:
+// Per-block partial sums of the diagnostics over (z, v) cells, each cell
+// weighted by its beam's quadrature weight over 2/nv:
 // [0] sum P0(nu) [1] sum P0(nubar) [2..4] sum P(S - Sbar^*) [5] max |dP|
 // [6] sum |dP_nu| P0_nu [7] sum P0_nu (cells with P0 > 0).
 __global__ void conserved_partial_kernel(const double* __restrict__ y, int64_t nz, int nv,
-                                         double* __restrict__ partial) {
+                                         double* __restrict__ partial, int vgrid) {
   __shared__ double red[8][kDiagBlock / 32];
   const int64_t ncell = nz * nv;
   double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < ncell;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t z = e / nv, j = e % nv;
+    // the beam's weight relative to the midpoint bin width 2/nv (1 for midpoint bins)
+    const double f = vgrid == kVgridMidpoint ? 1.0 : vgrid_w((int)j, nv, vgrid) * (0.5 * nv);
     double P[2][4];
 #pragma unroll
     for (int s = 0; s < 2; ++s) {
@@ -187,16 +259,16 @@ __global__ void conserved_partial_kernel(const double* __restrict__ y, int64_t n
         const double dp = fabs(len / P[s][0] - 1.0);
         acc[5] = fmax(acc[5], dp);
         if (s == 0) {
-          acc[6] += dp * P[s][0];
-          acc[7] += P[s][0];
+          acc[6] += f * (dp * P[s][0]);
+          acc[7] += f * P[s][0];
         }
       }
     }
-    acc[0] += P[0][0];
-    acc[1] += P[1][0];
-    acc[2] += P[0][1] - P[1][1];
-    acc[3] += P[0][2] + P[1][2];  // conjugation flips P2 of Sbar
-    acc[4] += P[0][3] - P[1][3];
+    acc[0] += f * P[0][0];
+    acc[1] += f * P[1][0];
+    acc[2] += f * (P[0][1] - P[1][1]);
+    acc[3] += f * (P[0][2] + P[1][2]);  // conjugation flips P2 of Sbar
+    acc[4] += f * (P[0][3] - P[1][3]);
   }
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "cosenu_device.cuh"
+
 namespace cosenu {
 
 constexpr int kDiagBlock = 256;
@@ -20,7 +22,7 @@ struct ApplySeg {
 };
 
 __global__ void ymoments_kernel(const double* __restrict__ y, int64_t nz, int nv,
-                                double* __restrict__ out, int stride);
+                                double* __restrict__ out, int stride, int vgrid);
 __global__ void y32_from_y_kernel(const double* __restrict__ y, float* __restrict__ y32,
                                   int64_t n);
 __global__ void apply_increment_kernel(double* __restrict__ y, float* __restrict__ y32,
@@ -33,10 +35,14 @@ __global__ void collective_fill_kernel(double* __restrict__ y, int64_t nz, int n
                                        const double* __restrict__ ph);
 __global__ void gather_flags_kernel(uint32_t* const* __restrict__ flags, int n,
                                     uint32_t* __restrict__ out, int clear);
+__global__ void dp_field_kernel(const double* __restrict__ y, int64_t nz, int nv,
+                                double* __restrict__ out);
+__global__ void dft_beam_kernel(const double* __restrict__ y, int64_t nz, int nv, int s, int j,
+                                int64_t m0, double* __restrict__ out);
 __global__ void zavg_kernel(const double* __restrict__ y, int64_t nz, int nv,
                             double* __restrict__ out);
 __global__ void conserved_partial_kernel(const double* __restrict__ y, int64_t nz, int nv,
-                                         double* __restrict__ partial);
+                                         double* __restrict__ partial, int vgrid);
 __global__ void conserved_final_kernel(const double* __restrict__ partial, int nblocks,
                                        double* __restrict__ out);
 

@@ -40,6 +40,7 @@ struct cosenu_s {
   int32_t nv = 0;
   double L = 0;
   int scheme = 0, precision = 0;
+  int vgrid = 0;  // velocity quadrature (COSENU_MIDPOINT, ...)
   cosenu_params p{};
   cudaStream_t stream = nullptr;
   bool own_stream = false;

@@ -36,12 +36,14 @@ MUTATIONS = {
     "KO r = 3 normalisation 2^6": ("(h * h * h * h * h) * dd[0] / 64.0;",
                                    "(h * h * h * h * h) * dd[0] / 32.0;"),
     "KO r = 3 sign (-1)^3": ("Qu = p->ko_eps * -1.0 /* (-1)^3 */", "Qu = p->ko_eps * 1.0 /* (-1)^3 */"),
+    "Simpson 3/8 end panel weight": ("    w[n - 2] += 9.0 * h / 8.0;", "    w[n - 2] += 8.0 * h / 8.0;"),
     "M2 sign": ("M[1] += wg[j] * h * (P[0][2] + P[1][2]);",
                 "M[1] += wg[j] * h * (P[0][2] - P[1][2]);"),
 }
 
 PINS = [
     (pins.test_vgrid_midpoints, {}),
+    (pins.test_vgrid_vertex_quadratures, {"nv": 12}),
     (pins.test_weno7_constant_data, {}),
     (pins.test_weno7_cubic_reconstructed_exactly, {"seed": 1}),
     (pins.test_weno7_linear_weights_reproduce_eq_f7, {}),

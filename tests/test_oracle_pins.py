@@ -69,6 +69,45 @@ def test_vgrid_midpoints(oracle):
     assert np.all(np.diff(v) > 0)
 
 
+@pytest.mark.parametrize("nv", [4, 8, 12, 9, 33])
+def test_vgrid_vertex_quadratures(oracle, nv):
+    """Sec. 3.1 vertex grids: v_j = -1 + j h on [-1, 1].  The trapezoid rule
+    integrates polynomials of degree <= 1 exactly and v^2 with the composite
+    error h^2 / 3; Simpson's rule (with a 3/8 panel closing an odd interval
+    count) integrates degree <= 3 exactly; all weights are positive."""
+    exact = [2.0, 0.0, 2.0 / 3.0, 0.0, 2.0 / 5.0]
+    h = 2.0 / (nv - 1)
+    v, w = oracle.vgrid(nv, oracle.TRAPEZOID)
+    assert v[0] == -1.0 and v[-1] == pytest.approx(1.0, abs=1e-15)
+    assert np.allclose(np.diff(v), h, atol=1e-15) and np.all(w > 0)
+    for k in (0, 1):
+        assert np.sum(w * v ** k) == pytest.approx(exact[k], abs=1e-14)
+    assert np.sum(w * v ** 2) == pytest.approx(2.0 / 3.0 + h * h / 3.0, abs=1e-14)
+    v, w = oracle.vgrid(nv, oracle.SIMPSON)
+    assert np.all(w > 0)
+    for k in range(4):
+        assert np.sum(w * v ** k) == pytest.approx(exact[k], abs=1e-14)
+    if (nv - 1) % 2 == 0:  # pure 1/3 rule: error of v^4 is -4 h^4 / 15
+        assert np.sum(w * v ** 4) == pytest.approx(exact[4] + 4.0 * h ** 4 / 15.0, abs=1e-14)
+    else:  # the 3/8 panel makes the rule no longer exact for v^4
+        assert abs(np.sum(w * v ** 4) - exact[4]) > 1e-8
+
+
+@pytest.mark.parametrize("mode", [1, 2])
+def test_moments_vertex_quadratures_exact_for_linear_profiles(oracle, mode):
+    """With S_ee - S_xx = 1 + v, D3_0 = int (1 + v) dv = 2 and D3_1 = int (v + v^2) dv
+    = 2/3 (Simpson, exact to degree 3) or 2/3 + h^2/3 (trapezoid)."""
+    nz, nv = 4, 12
+    v, _ = oracle.vgrid(nv, mode)
+    u = np.zeros((2, 4, nz, nv))
+    u[0, 0] = (1 + v)[None, :]
+    _, vmom = oracle.moments(oracle.params(nz, nv, 1.0, vgrid=mode), u)
+    h = 2.0 / (nv - 1)
+    assert np.allclose(vmom[:, 0], 2.0, atol=1e-14)
+    d31 = 2.0 / 3.0 + (h * h / 3.0 if mode == 1 else 0.0)
+    assert np.allclose(vmom[:, 1], d31, atol=1e-14)
+
+
 # --------------------------------------------------------------------------- WENO7
 
 

@@ -154,3 +154,101 @@ def test_box_car_gibbs_fd_versus_weno():
         over[scheme] = max(st[0, 0].max() - 1.0, -st[0, 0].min())
     assert over[FD] > 0.05
     assert over[WENO] < 0.25 * over[FD]
+
+
+def test_dp_field_and_spectrum_diagnostics():
+    """Sec. 5 diagnostics on the device: the delta P(z, v) map and the z-Fourier
+    spectrum of a beam's perpendicular polarisation, against numpy on the state
+    read back."""
+    nz, nv, L = 300, 32, 180.0
+    u0 = inputs.gaussian_perturbation_state(nz, nv, L)
+    with binding.Solver(nz, nv, L, WENO, FP64, mu=1.0, dt=0.2 * L / nz) as s:
+        s.set_state(u0)
+        s.step(200)
+        s.sync()
+        st = s.state()
+        dp = binding.cosenu_dp_field(s.h, nz, nv)
+        for sp, j, m0, nk in [(0, nv - 1, -40, 81), (1, 3, 0, nz), (0, 10, 250, 60)]:
+            X = binding.cosenu_spectrum(s.h, sp, j, m0, nk)
+            x = 2.0 * st[sp, 2, :, j] - 2j * st[sp, 3, :, j]
+            ref = np.fft.fft(x)[(np.arange(m0, m0 + nk)) % nz]
+            assert np.max(np.abs(X - ref)) <= 1e-12 * np.sum(np.abs(x))
+        with pytest.raises(binding.CosenuError):
+            binding.cosenu_spectrum(s.h, 2, 0, 0, 1)
+        with pytest.raises(binding.CosenuError):
+            binding.cosenu_spectrum(s.h, 0, nv, 0, 1)
+    for sp in range(2):
+        P, p0 = bloch(st[sp])
+        ref = np.linalg.norm(P, axis=0) / p0 - 1.0
+        assert np.max(np.abs(dp[sp] - ref)) <= 1e-14
+
+
+TRAP, SIMP = binding.COSENU_TRAPEZOID, binding.COSENU_SIMPSON
+
+
+def run_gpu_q(u0, L, scheme, prec, nsteps, vgrid, **params):
+    nz, nv = u0.shape[2], u0.shape[3]
+    with binding.Solver(nz, nv, L, scheme, prec, **params) as s:
+        binding.cosenu_set_quadrature(s.h, vgrid)
+        s.set_state(u0)
+        s.step(nsteps)
+        s.sync()
+        return s.state(), s.conserved(), s.moments()
+
+
+@pytest.mark.parametrize("vgrid", [TRAP, SIMP])
+@pytest.mark.parametrize("scheme", [FD, WENO])
+@pytest.mark.parametrize("prec", [FP64, MIXED])
+def test_vertex_quadrature_parity(vgrid, scheme, prec, oracle):
+    """Sec. 3.1 vertex grids with the trapezoid and Simpson rules, all terms
+    active, against the oracle (FP64 1e-12; mixed 1e-5 of each component's scale)."""
+    nz, nv, L = 64, 16, 12.0
+    u0 = inputs.random_state(nz, nv, seed=40 + vgrid, offdiag=0.05)
+    kw = dict(mu=1.2, omega=0.3, theta=0.2)
+    got, cons, (zavg, vmom) = run_gpu_q(u0, L, scheme, prec, 6, vgrid, **kw)
+    p = oracle.params(nz, nv, L, scheme, vgrid=vgrid, **kw)
+    ref = oracle.step(p, u0, 6)
+    if prec == FP64:
+        assert max_abs(got, ref) <= 1e-12
+        oc = oracle.conserved(p, ref)
+        assert cons["tr_nu"] == pytest.approx(oc["tr_nu"], rel=1e-13)
+        assert np.allclose(cons["M"], oc["M"], rtol=1e-12, atol=1e-13)
+        assert cons["dP_mean"] == pytest.approx(oc["dP_mean"], rel=1e-12, abs=1e-15)
+        oz, om = oracle.moments(p, ref)
+        assert np.max(np.abs(vmom - om)) <= 1e-13
+    else:
+        from parity_util import rel_by_component
+        assert rel_by_component(got, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("vgrid", [binding.COSENU_MIDPOINT, TRAP, SIMP])
+def test_velocities_and_collective_normalisation(vgrid, oracle):
+    nz, nv = 16, 12
+    with binding.Solver(nz, nv, 3.0, FD, FP64) as s:
+        binding.cosenu_set_quadrature(s.h, vgrid)
+        v, w = binding.cosenu_velocities(s.h, nv)
+        ov, ow = oracle.vgrid(nv, vgrid)
+        assert np.allclose(v, ov, atol=1e-15) and np.allclose(w, ow, atol=1e-15)
+        binding.cosenu_set_state_collective(s.h, alpha=0.8, sigma_nu=0.6, sigma_nubar=0.5)
+        st = s.state()
+    assert np.sum(w * st[0, 0, 3]) == pytest.approx(1.0, abs=1e-14)
+    assert np.sum(w * st[1, 0, 3]) == pytest.approx(0.8, abs=1e-14)
+
+
+def test_batch_with_mixed_quadratures_bitwise():
+    specs = [(120, 16, FD, MIXED, TRAP), (80, 16, FD, MIXED, binding.COSENU_MIDPOINT),
+             (64, 32, WENO, FP64, SIMP), (200, 16, FD3, MIXED, SIMP)]
+    states = [inputs.random_state(nz, nv, seed=60 + i, offdiag=0.05)
+              for i, (nz, nv, *_) in enumerate(specs)]
+    refs = [run_gpu_q(u0, 0.2 * nz, sc, pr, 5, vg, mu=1.5)[0]
+            for u0, (nz, nv, sc, pr, vg) in zip(states, specs)]
+    with binding.Batch() as b:
+        ms = []
+        for u0, (nz, nv, sc, pr, vg) in zip(states, specs):
+            m = b.add(nz, nv, 0.2 * nz, sc, pr, mu=1.5)
+            binding.cosenu_set_quadrature(m.h, vg)
+            m.set_state(u0)
+            ms.append(m)
+        b.step(5)
+        for m, r in zip(ms, refs):
+            assert np.array_equal(m.state(), r)
