@@ -55,6 +55,7 @@ Layout make_layout(int64_t nz, int32_t nv, int precision) {
   L.d3 = off; off = align_up(off + n * dsz);
   L.my = off; off = align_up(off + (size_t)nz * 8 * sizeof(double));
   L.zavg = off; off = align_up(off + (size_t)8 * nv * sizeof(double));
+  L.vtab = off; off = align_up(off + (size_t)2 * nv * sizeof(double));
   L.partial = off; off = align_up(off + (size_t)kDiagMaxBlocks * 8 * sizeof(double));
   L.result = off; off = align_up(off + 8 * sizeof(double));
   L.err = off; off = align_up(off + 64);
@@ -191,7 +192,7 @@ int slot_bytes_of(int precision, int nv, int stage, int rows) {
 // missing buffer is refused instead of faulting on the device).
 bool stage_args_complete(int precision, int stage, const StageArgs& a) {
   const bool mixed = precision == COSENU_MIXED;
-  if (!a.err || (mixed ? !a.y32_in || !a.my : !a.y_in)) return false;
+  if (!a.err || !a.vtab || (mixed ? !a.y32_in || !a.my : !a.y_in)) return false;
   if (stage > 1 && !a.d_in) return false;
   if ((stage < 4 || mixed) && !a.d_out) return false;
   if (stage == 4 && (!a.d1 || !a.d2 || (!mixed && !a.y_out))) return false;
@@ -273,7 +274,7 @@ StageArgs stage_args(const cosenu_s* h, int stage, int ycur) {
   a.ring = h->cfg[stage].ring;
   a.rows_per_slot = h->cfg[stage].rows_per_slot;
   a.slot_bytes = h->cfg[stage].slot_bytes;
-  a.vgrid = h->vgrid;
+  a.vtab = h->vtab;
   a.inv_dz = (double)h->nz / h->L;
   a.dt = h->p.dt;
   a.mu = h->p.mu;
@@ -382,6 +383,20 @@ void default_params(cosenu_t h) {
   h->p.dt = 0.4 * h->L / (double)h->nz;
 }
 
+// The beam velocities and weights of the handle's quadrature into its device
+// table (the stage kernels read them once per column).
+cudaError_t upload_vtab(cosenu_t h) {
+  std::vector<double> t((size_t)2 * h->nv);
+  for (int j = 0; j < h->nv; ++j) {
+    t[j] = vgrid_v(j, h->nv, h->vgrid);
+    t[(size_t)h->nv + j] = vgrid_w(j, h->nv, h->vgrid);
+  }
+  cudaError_t e = cudaMemcpyAsync(h->vtab, t.data(), t.size() * sizeof(double),
+                                  cudaMemcpyHostToDevice, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // t dies here
+  return e;
+}
+
 cosenu_t create_common(int64_t nz, int32_t nv, double L, int scheme, int precision,
                        void* workspace, size_t ws_bytes, cudaStream_t stream = nullptr) {
   if (!valid_sizes(nz, nv, scheme, precision) || !(L > 0.0) || !std::isfinite(L)) {
@@ -441,9 +456,11 @@ cosenu_t create_common(int64_t nz, int32_t nv, double L, int scheme, int precisi
   h->d[2] = h->ws + h->lay.d3;
   h->my = reinterpret_cast<double*>(h->ws + h->lay.my);
   h->err = reinterpret_cast<uint32_t*>(h->ws + h->lay.err);
+  h->vtab = reinterpret_cast<double*>(h->ws + h->lay.vtab);
   if (configure(h) != COSENU_OK) return bail("launch configuration failed", COSENU_ECUDA);
   e = cudaMemsetAsync(h->ws, 0, h->lay.total, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  if (e == cudaSuccess) e = upload_vtab(h);
   if (e != cudaSuccess) return bail(std::string("memset: ") + cudaGetErrorString(e), COSENU_ECUDA);
   return h;
 }
@@ -551,9 +568,11 @@ int cosenu_set_quadrature(cosenu_t h, int32_t mode) {
   if (mode != COSENU_MIDPOINT && mode != COSENU_TRAPEZOID && mode != COSENU_SIMPSON)
     return fail(h, COSENU_EINVAL, "unknown quadrature");
   if (mode == h->vgrid) return COSENU_OK;
+  CK(h, cudaStreamSynchronize(h->stream));  // queued steps read the old table
   h->vgrid = mode;
   ++h->version;
   drop_graph(h);
+  CK(h, upload_vtab(h));
   CK(h, refresh_moments(h));  // the mixed path's running moments use the weights
   return COSENU_OK;
 }

@@ -39,7 +39,6 @@ struct StageArgs {
   int32_t ring;           // bulk-copy ring depth (slots)
   int32_t rows_per_slot;  // consecutive z rows per ring slot (one bulk copy per plane)
   int32_t slot_bytes;     // bytes of one ring slot
-  int32_t vgrid;          // velocity quadrature (kVgrid*)
   double inv_dz;          // 1 / dz
   double dt;
   double mu;
@@ -56,6 +55,7 @@ struct StageArgs {
   const void* d1;         // stage 4: delta_1 (center rows only)
   const void* d2;         // stage 4: delta_2 (center rows only)
   double* my;             // mixed: running FP64 moments of y, [nz][8] (6 used)
+  const double* vtab;     // beam velocities v_j [nv], then quadrature weights w_j [nv]
   uint32_t* err;          // device error flags
 };
 

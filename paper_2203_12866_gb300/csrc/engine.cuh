@@ -22,7 +22,7 @@ struct StageCfg {
 
 // Byte offsets of a handle's buffers inside its workspace.
 struct Layout {
-  size_t y0, y1, y32a, y32b, d1, d2, d3, my, zavg, partial, result, err, total;
+  size_t y0, y1, y32a, y32b, d1, d2, d3, my, zavg, vtab, partial, result, err, total;
 };
 
 // One admissible ring shape of a stage kernel: R rows per slot, D slots.
@@ -52,6 +52,7 @@ struct cosenu_s {
   int ycur = 0;
   void* d[3] = {nullptr, nullptr, nullptr};
   double* my = nullptr;
+  double* vtab = nullptr;  // beam velocities [nv] and quadrature weights [nv]
   uint32_t* err = nullptr;
   cosenu::StageCfg cfg[5];
   int nsm = 0;
