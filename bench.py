@@ -51,10 +51,9 @@ WORKLOAD = ("roofline run: nz=2^20, nv=256, z in [-25600,25600), dt=0.4 dz, mu=1
 #   writes d2; stage 3 reads y, d2, writes d3; stage 4 reads y, d3, d1, d2 and
 #   writes the new y.
 # mixed (state y double plus its float copy y32; increments float): stages 1-3
-#   read y32 instead of y; stage 4 reads y32, d3 (window), d1, d2 (center) and
-#   writes the float increment dy; the increment kernel reads y, dy and writes
-#   y, y32.
-STAGE_BYTES = {"fp64": (16, 24, 24, 40, 0), "mixed": (8, 12, 12, 20, 24)}
+#   read y32 instead of y; stage 4 reads y32, d3 and writes d4; the increment
+#   kernel reads y, d1, d2, d3, d4 and writes y, y32.
+STAGE_BYTES = {"fp64": (16, 24, 24, 40, 0), "mixed": (8, 12, 12, 12, 36)}
 KERNEL_NAMES = ("stage 1", "stage 2", "stage 3", "stage 4", "increment")
 # Algorithmic FP64 flops per cell (4 reals) per launch of the fp64 stages
 # (moments, Hamiltonian, commutator, stencil, RK axpy; FMA = 2 flops).

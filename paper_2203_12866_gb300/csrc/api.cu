@@ -53,7 +53,11 @@ Layout make_layout(int64_t nz, int32_t nv, int precision) {
   L.d1 = off; off = align_up(off + n * dsz);
   L.d2 = off; off = align_up(off + n * dsz);
   L.d3 = off; off = align_up(off + n * dsz);
+  const size_t n4 = precision == COSENU_MIXED ? n : 0;  // delta_4 (mixed)
+  L.d4 = off; off = align_up(off + n4 * dsz);
   L.my = off; off = align_up(off + (size_t)nz * 8 * sizeof(double));
+  const size_t nmd = precision == COSENU_MIXED ? (size_t)2 * nz * 8 : 0;
+  L.mdel = off; off = align_up(off + nmd * sizeof(float));
   L.zavg = off; off = align_up(off + (size_t)8 * nv * sizeof(double));
   L.vtab = off; off = align_up(off + (size_t)2 * nv * sizeof(double));
   L.partial = off; off = align_up(off + (size_t)kDiagMaxBlocks * 8 * sizeof(double));
@@ -192,10 +196,10 @@ int slot_bytes_of(int precision, int nv, int stage, int rows) {
 // missing buffer is refused instead of faulting on the device).
 bool stage_args_complete(int precision, int stage, const StageArgs& a) {
   const bool mixed = precision == COSENU_MIXED;
-  if (!a.err || !a.vtab || (mixed ? !a.y32_in || !a.my : !a.y_in)) return false;
+  if (!a.err || !a.vtab || (mixed ? !a.y32_in || !a.my || !a.mdel : !a.y_in)) return false;
   if (stage > 1 && !a.d_in) return false;
   if ((stage < 4 || mixed) && !a.d_out) return false;
-  if (stage == 4 && (!a.d1 || !a.d2 || (!mixed && !a.y_out))) return false;
+  if (stage == 4 && !mixed && (!a.d1 || !a.d2 || !a.y_out)) return false;
   return true;
 }
 
@@ -287,13 +291,14 @@ StageArgs stage_args(const cosenu_s* h, int stage, int ycur) {
   a.y_out = h->y[ycur ^ 1];
   a.y32_in = h->y32[0];
   a.my = h->my;
+  a.mdel = h->mdel;
   a.err = h->err;
   switch (stage) {
     case 1: a.d_out = h->d[0]; break;
     case 2: a.d_in = h->d[0]; a.d_out = h->d[1]; break;
     case 3: a.d_in = h->d[1]; a.d_out = h->d[2]; break;
-    default:  // mixed: the increment dy overwrites delta_1 (read by this CTA only)
-      a.d_in = h->d[2]; a.d1 = h->d[0]; a.d2 = h->d[1]; a.d_out = h->d[0]; break;
+    default:  // FP64: y from the center rows of delta_1, delta_2; mixed: delta_4
+      a.d_in = h->d[2]; a.d1 = h->d[0]; a.d2 = h->d[1]; a.d_out = h->d[3]; break;
   }
   return a;
 }
@@ -315,7 +320,8 @@ cudaError_t launch_apply(cosenu_t h) {
   const int64_t n = 8 * h->nz * (int64_t)h->nv;
   const int64_t blocks = std::min<int64_t>((n / 4 + 255) / 256, (int64_t)h->nsm * 8);
   apply_increment_kernel<<<(int)blocks, 256, 0, h->stream>>>(
-      h->y[0], h->y32[0], static_cast<const float*>(h->d[0]), n, h->err);
+      h->y[0], h->y32[0], static_cast<const float*>(h->d[0]), static_cast<const float*>(h->d[1]),
+      static_cast<const float*>(h->d[2]), static_cast<const float*>(h->d[3]), n, h->err);
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
   return e;
@@ -454,6 +460,10 @@ cosenu_t create_common(int64_t nz, int32_t nv, double L, int scheme, int precisi
   h->d[0] = h->ws + h->lay.d1;
   h->d[1] = h->ws + h->lay.d2;
   h->d[2] = h->ws + h->lay.d3;
+  if (precision == COSENU_MIXED) {
+    h->d[3] = h->ws + h->lay.d4;
+    h->mdel = reinterpret_cast<float*>(h->ws + h->lay.mdel);
+  }
   h->my = reinterpret_cast<double*>(h->ws + h->lay.my);
   h->err = reinterpret_cast<uint32_t*>(h->ws + h->lay.err);
   h->vtab = reinterpret_cast<double*>(h->ws + h->lay.vtab);

@@ -213,7 +213,7 @@ int write_tables(cosenu_batch_t b) {
         ApplySeg sg;
         sg.y = h->y[0];
         sg.y32 = h->y32[0];
-        sg.dy = static_cast<const float*>(h->d[0]);
+        for (int k = 0; k < 4; ++k) sg.d[k] = static_cast<const float*>(h->d[k]);
         sg.n4 = 2 * h->nz * (int64_t)h->nv;
         sg.err = h->err;
         segs.push_back(sg);

@@ -57,8 +57,17 @@ __global__ void y32_from_y_kernel(const double* __restrict__ y, float* __restric
     y32[e] = d2f_rn_int(y[e]);
 }
 
-// y[0..3] += dy (in double), returns false if a result is not finite, and
-// writes the float copy of the four results.
+// The step's float increment of four reals from the stage increments,
+// (delta_1 + 2 delta_2 + delta_3) / 3 + delta_4 / 6 (classic RK4 with
+// delta_1,2 = dt/2 k_1,2 and delta_3,4 = dt k_3,4); then y[0..3] += it in
+// double and the float copy of the four results.  Returns false if a result is
+// not finite.
+__device__ __forceinline__ float4 rk4_increment(float4 a, float4 b, float4 c, float4 d) {
+  const float t = 1.0f / 3.0f, s = 1.0f / 6.0f;
+  return make_float4((a.x + 2.0f * b.x + c.x) * t + d.x * s, (a.y + 2.0f * b.y + c.y) * t + d.y * s,
+                     (a.z + 2.0f * b.z + c.z) * t + d.z * s, (a.w + 2.0f * b.w + c.w) * t + d.w * s);
+}
+
 __device__ __forceinline__ bool apply4(double2* __restrict__ y, float4* __restrict__ y32,
                                        float4 d) {
   double2 a = y[0];
@@ -73,19 +82,37 @@ __device__ __forceinline__ bool apply4(double2* __restrict__ y, float4* __restri
   return is_finite_bits(a.x) && is_finite_bits(a.y) && is_finite_bits(b.x) && is_finite_bits(b.y);
 }
 
-// Mixed path, end of an RK4 step: y <- y + dy in double (dy is the float
-// increment written by stage 4) and the float copy y32 <- round(y), in place,
-// element by element.  n = 8 nz nv (a multiple of 4).
-__global__ void __launch_bounds__(256) apply_increment_kernel(double* __restrict__ y,
-                                                               float* __restrict__ y32,
-                                                               const float* __restrict__ dy,
-                                                               int64_t n, uint32_t* err) {
+// Mixed path, end of an RK4 step: y <- y + increment in double and the float
+// copy y32 <- round(y), in place, element by element.  d1..d4 are the float
+// stage increments; n = 8 nz nv (a multiple of 4).
+__global__ void __launch_bounds__(256) apply_increment_kernel(
+    double* __restrict__ y, float* __restrict__ y32, const float* __restrict__ d1,
+    const float* __restrict__ d2, const float* __restrict__ d3, const float* __restrict__ d4,
+    int64_t n, uint32_t* err) {
   bool bad = false;
   const int64_t n4 = n >> 2;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4;
-       i += (int64_t)gridDim.x * blockDim.x)
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // two float4 groups per thread and iteration: more loads in flight
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += 2 * stride) {
+    const int64_t i2 = i + stride;
+    const bool two = i2 < n4;
+    const float4 a1 = reinterpret_cast<const float4*>(d1)[i];
+    const float4 a2 = reinterpret_cast<const float4*>(d2)[i];
+    const float4 a3 = reinterpret_cast<const float4*>(d3)[i];
+    const float4 a4 = reinterpret_cast<const float4*>(d4)[i];
+    float4 b1 = a1, b2 = a2, b3 = a3, b4 = a4;
+    if (two) {
+      b1 = reinterpret_cast<const float4*>(d1)[i2];
+      b2 = reinterpret_cast<const float4*>(d2)[i2];
+      b3 = reinterpret_cast<const float4*>(d3)[i2];
+      b4 = reinterpret_cast<const float4*>(d4)[i2];
+    }
     bad |= !apply4(reinterpret_cast<double2*>(y) + 2 * i, reinterpret_cast<float4*>(y32) + i,
-                   reinterpret_cast<const float4*>(dy)[i]);
+                   rk4_increment(a1, a2, a3, a4));
+    if (two)
+      bad |= !apply4(reinterpret_cast<double2*>(y) + 2 * i2, reinterpret_cast<float4*>(y32) + i2,
+                     rk4_increment(b1, b2, b3, b4));
+  }
   if (__ballot_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, kErrNonFinite);
 }
 
@@ -106,10 +133,14 @@ __global__ void __launch_bounds__(256) apply_increment_batch_kernel(
     const int64_t i0 = (ch - chunk_first[lo]) * kApplyChunk4;
     const int64_t i1 = min(sg.n4, i0 + kApplyChunk4);
     bool bad = false;
-    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x)
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+      const float4 inc = rk4_increment(reinterpret_cast<const float4*>(sg.d[0])[i],
+                                       reinterpret_cast<const float4*>(sg.d[1])[i],
+                                       reinterpret_cast<const float4*>(sg.d[2])[i],
+                                       reinterpret_cast<const float4*>(sg.d[3])[i]);
       bad |= !apply4(reinterpret_cast<double2*>(sg.y) + 2 * i,
-                     reinterpret_cast<float4*>(sg.y32) + i,
-                     reinterpret_cast<const float4*>(sg.dy)[i]);
+                     reinterpret_cast<float4*>(sg.y32) + i, inc);
+    }
     if (__ballot_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0)
       atomicOr(sg.err, kErrNonFinite);
   }

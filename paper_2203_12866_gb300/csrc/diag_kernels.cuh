@@ -16,7 +16,7 @@ constexpr int64_t kApplyChunk4 = 1024;  // float4 groups per chunk of the batche
 struct ApplySeg {
   double* y;
   float* y32;
-  const float* dy;
+  const float* d[4];  // the four stage increments
   int64_t n4;
   uint32_t* err;
 };
@@ -26,7 +26,9 @@ __global__ void ymoments_kernel(const double* __restrict__ y, int64_t nz, int nv
 __global__ void y32_from_y_kernel(const double* __restrict__ y, float* __restrict__ y32,
                                   int64_t n);
 __global__ void apply_increment_kernel(double* __restrict__ y, float* __restrict__ y32,
-                                       const float* __restrict__ dy, int64_t n, uint32_t* err);
+                                       const float* __restrict__ d1, const float* __restrict__ d2,
+                                       const float* __restrict__ d3, const float* __restrict__ d4,
+                                       int64_t n, uint32_t* err);
 __global__ void apply_increment_batch_kernel(const ApplySeg* __restrict__ segs,
                                              const int64_t* __restrict__ chunk_first, int nseg,
                                              int64_t nchunks);

@@ -22,7 +22,7 @@ struct StageCfg {
 
 // Byte offsets of a handle's buffers inside its workspace.
 struct Layout {
-  size_t y0, y1, y32a, y32b, d1, d2, d3, my, zavg, vtab, partial, result, err, total;
+  size_t y0, y1, y32a, y32b, d1, d2, d3, d4, my, mdel, zavg, vtab, partial, result, err, total;
 };
 
 // One admissible ring shape of a stage kernel: R rows per slot, D slots.
@@ -50,8 +50,9 @@ struct cosenu_s {
   double* y[2] = {nullptr, nullptr};
   float* y32[2] = {nullptr, nullptr};  // mixed: float copy of y[0]
   int ycur = 0;
-  void* d[3] = {nullptr, nullptr, nullptr};
+  void* d[4] = {nullptr, nullptr, nullptr, nullptr};  // delta_1..3 (mixed: and delta_4)
   double* my = nullptr;
+  float* mdel = nullptr;   // mixed: float moments of delta_1, delta_2 per row
   double* vtab = nullptr;  // beam velocities [nv] and quadrature weights [nv]
   uint32_t* err = nullptr;
   cosenu::StageCfg cfg[5];

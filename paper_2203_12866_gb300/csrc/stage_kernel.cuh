@@ -128,8 +128,8 @@ __device__ __forceinline__ void vstore(T* p, const T (&in)[N]) {
 // Byte layout of one ring slot.  A slot carries R consecutive z rows: for each
 // array, the R rows of component plane q are contiguous ([q][r][v]) because
 // they are contiguous in global memory, so one bulk copy moves R rows of a
-// plane.  Window arrays belong to the leading rows i, center arrays (stage 4
-// only) to the rows i - lag.
+// plane.  Window arrays belong to the leading rows i, center arrays (FP64
+// stage 4 only) to the rows i - lag.
 struct SlotLayout {
   int y_off, din_off, yc_off, d1c_off, d2c_off, my_off, bytes;
 };
@@ -149,10 +149,10 @@ __host__ __device__ inline SlotLayout slot_layout(int nv, int stage, int R) {
   if (stage > 1) off += row_d;
   L.yc_off = off;
   if (stage == 4 && PREC == kFP64) off += row_y;
-  L.d1c_off = off;
-  if (stage == 4) off += row_d;
+  L.d1c_off = off;  // FP64 stage 4 only (the mixed stage 4 writes delta_4 instead)
+  if (stage == 4 && PREC == kFP64) off += row_d;
   L.d2c_off = off;
-  if (stage == 4) off += row_d;
+  if (stage == 4 && PREC == kFP64) off += row_d;
   L.my_off = off;
   if (PREC == kMIXED) off += 8 * (int)sizeof(double) * R;
   L.bytes = (off + 127) & ~127;
