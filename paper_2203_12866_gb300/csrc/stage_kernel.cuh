@@ -308,6 +308,16 @@ __host__ __device__ constexpr int stage_max_threads() {
   return (stage_max_consumer_warps<SCHEME, PREC, STAGE>() + 2) * 32;
 }
 
+// Minimum resident CTAs per SM the compiler is told to allow for.  The mixed
+// FD4+KO kernels are left to the compiler's own register budget (two 320-thread
+// CTAs per SM at 96 registers, which streams fastest); the FP64 and WENO7
+// kernels run one CTA per SM and are faster with the whole per-CTA budget
+// (measured: mixed WENO7 stage 1 15.5 -> 11.8 ms, FP64 FD4+KO 335 -> 331 ms per step).
+template <int SCHEME, int PREC, int STAGE>
+__host__ __device__ constexpr int stage_min_blocks() {
+  return (SCHEME != kWENO7 && PREC == kMIXED) ? 0 : 1;
+}
+
 // Shared memory of a stage kernel besides its ring slots.
 template <int SCHEME, int PREC, int STAGE>
 __host__ __device__ constexpr int stage_smem_header_bytes() {
@@ -336,7 +346,8 @@ struct BatchTable {
 // their own parameters, share one launch; every cell sees the same arithmetic
 // as in a single-grid launch.
 template <int SCHEME, int PREC, int STAGE, bool BATCHED>
-__global__ void __launch_bounds__(stage_max_threads<SCHEME, PREC, STAGE>())
+__global__ void __launch_bounds__(stage_max_threads<SCHEME, PREC, STAGE>(),
+                                  stage_min_blocks<SCHEME, PREC, STAGE>())
     rk4_stage_kernel(const StageArgs a, const BatchTable bt) {
   if constexpr (BATCHED) {
     const WorkItem w = bt.items[blockIdx.x];
