@@ -6,10 +6,10 @@
 //         - i [H(u_s), u_s]                                 (Eq. (eom), (ham))
 //   delta_1 = dt/2 k_1, delta_2 = dt/2 k_2, delta_3 = dt k_3,
 //   y <- y + (delta_1 + 2 delta_2 + delta_3) / 3 + dt/6 k_4   (classic RK4)
-// In the mixed path stage 4 writes the float increment
-//   dy = (delta_1 + 2 delta_2 + delta_3) / 3 + dt/6 k_4
-// (over delta_1, which only this CTA reads at those rows) and a separate
-// streaming kernel, apply_increment_kernel, performs y <- y + dy in double.
+// In the mixed path stage 4 writes delta_4 = dt k_4 like the other stages, and
+// a separate streaming kernel, apply_increment_kernel, forms
+//   dy = (delta_1 + 2 delta_2 + delta_3) / 3 + delta_4 / 6
+// in float and performs y <- y + dy in double.
 //
 // Work decomposition.  A CTA owns a contiguous range of z rows and all 2 nv
 // (species, v) columns, and marches along z with three warp roles:
@@ -161,8 +161,8 @@ __host__ __device__ inline SlotLayout slot_layout(int nv, int stage, int R) {
 
 // Shared memory besides the ring.  Acc is the type of the moment partials.
 //   mbarriers: full[kMaxRing] empty[kMaxRing] part[kMomSlots] mom[kMomSlots] dy[kMomSlots]
-//   flags (abort), partials [kMomSlots][NW consumer warps][8] Acc, dy partials (mixed
-//   only, same shape), finished moments [kMomSlots][8] Acc, running moments of
+//   flags (abort), partials [kMomSlots][NW consumer warps][8] Acc, delta_4 moment
+//   partials (mixed only, same shape), finished moments [kMomSlots][8] Acc, running moments of
 //   y (mixed) [kMomSlots][8] double.
 template <int PREC, int NW>
 struct SmemHeader {
