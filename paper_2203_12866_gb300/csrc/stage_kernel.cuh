@@ -245,58 +245,58 @@ __device__ __forceinline__ double weno7_face(double fm3, double fm2, double fm1,
   return num / (a0 + a1 + a2 + a3);
 }
 
-// Smoothness indicators of Eq. (Si4) as sums of squares.  SI_r is 240 times the
+// float: the same reconstruction written in the first, second and third
+// differences of the seven values,
+//   e_k = f_{k+1} - f_k (k = -3..2), g_k = e_{k+1} - e_k, h_k = g_{k+1} - g_k.
+// Candidate values (Eq. (f4s)): f4_r = f_0 + delta_r with
+//   delta_0 = 3/4 e_0 - 1/3 e_1 + 1/12 e_2     delta_1 = 1/12 e_-1 + 1/2 e_0 - 1/12 e_1
+//   delta_2 = -1/12 e_-2 + 1/3 e_-1 + 1/4 e_0  delta_3 = 1/4 e_-3 - 5/6 e_-2 + 13/12 e_-1.
+// Smoothness indicators (Eq. (Si4)) as sums of squares: SI_r is 240 times the
 // Jiang-Shu integral of the squared first three derivatives of the sub-stencil's
-// cubic; with the cubic's derivative coefficients that integral is
-//   (b1 + b3/4)^2 + (13/3) b2^2 + (781/20) b3^2,
-// which in integer differences of the four values reads
-//   SI = (20/3) D1^2 + 260 D2^2 + (781/3) D3^2
-// (D1: one-sided first difference x 6, D2: second difference, D3: third
-// difference; exact rational identity with the printed quadratic forms).  In
-// float the printed forms lose ~1e-3 (coefficients up to 1.7e4 times values of
-// order one) to cancellation, enough to turn an indicator negative and bring
-// SI + eps to zero; the squares keep every indicator >= 0 to full precision.
-__device__ __forceinline__ void weno7_si_sos(float fm3, float fm2, float fm1, float f0, float fp1,
-                                             float fp2, float fp3, float (&si)[4]) {
-  const float c1 = 20.0f / 3.0f, c2 = 260.0f, c3 = 781.0f / 3.0f;
-  const float s0a = -11.0f * f0 + 18.0f * fp1 - 9.0f * fp2 + 2.0f * fp3;
-  const float s0b = 2.0f * f0 - 5.0f * fp1 + 4.0f * fp2 - fp3;
-  const float s0c = -f0 + 3.0f * fp1 - 3.0f * fp2 + fp3;
-  const float s1a = -2.0f * fm1 - 3.0f * f0 + 6.0f * fp1 - fp2;
-  const float s12b = fm1 - 2.0f * f0 + fp1;  // shared by the two central sub-stencils
-  const float s1c = -fm1 + 3.0f * f0 - 3.0f * fp1 + fp2;
-  const float s2a = fm2 - 6.0f * fm1 + 3.0f * f0 + 2.0f * fp1;
-  const float s2c = -fm2 + 3.0f * fm1 - 3.0f * f0 + fp1;
-  const float s3a = -2.0f * fm3 + 9.0f * fm2 - 18.0f * fm1 + 11.0f * f0;
-  const float s3b = 2.0f * f0 - 5.0f * fm1 + 4.0f * fm2 - fm3;
-  const float s3c = -fm3 + 3.0f * fm2 - 3.0f * fm1 + f0;
-  si[0] = c1 * s0a * s0a + c2 * s0b * s0b + c3 * s0c * s0c;
-  si[1] = c1 * s1a * s1a + c2 * s12b * s12b + c3 * s1c * s1c;
-  si[2] = c1 * s2a * s2a + c2 * s12b * s12b + c3 * s2c * s2c;
-  si[3] = c1 * s3a * s3a + c2 * s3b * s3b + c3 * s3c * s3c;
-}
-
-// float: indicators as sums of squares, fast reciprocals (the mixed path's
-// weights need no more).
+// cubic, which in these differences reads
+//   SI_r = (20/3) a_r^2 + 260 b_r^2 + (781/3) c_r^2,
+//   a = (11 e_0 - 7 e_1 + 2 e_2, 2 e_-1 + 5 e_0 - e_1, -e_-2 + 5 e_-1 + 2 e_0,
+//        2 e_-3 - 7 e_-2 + 11 e_-1)           (6 x the cubic's slope at f_0's face)
+//   b = (2 g_0 - g_1, g_-1, g_-1, 2 g_-2 - g_-3),  c = (h_0, h_-1, h_-2, h_-3)
+// (exact rational identities with the printed forms).  In float the printed
+// forms lose ~1e-3 (coefficients up to 1.7e4 times values of order one) to
+// cancellation, enough to turn an indicator negative and bring SI + eps to
+// zero; the squares keep every indicator >= 0 to full precision, and the
+// differences make the reconstruction about a quarter cheaper.  The square
+// roots of 20/3 and 260 are folded into the coefficients of a and b.
+// Weights Eq. (weight) with fast reciprocals (the mixed path's weights need no more).
 __device__ __forceinline__ float weno7_face(float fm3, float fm2, float fm1, float f0, float fp1,
                                             float fp2, float fp3, float eps) {
-  const float c12 = 1.0f / 12.0f;
-  float f4[4], si[4];
-  f4[0] = (3.0f * f0 + 13.0f * fp1 - 5.0f * fp2 + fp3) * c12;
-  f4[1] = (-fm1 + 7.0f * f0 + 7.0f * fp1 - fp2) * c12;
-  f4[2] = (fm2 - 5.0f * fm1 + 13.0f * f0 + 3.0f * fp1) * c12;
-  f4[3] = (-3.0f * fm3 + 13.0f * fm2 - 23.0f * fm1 + 25.0f * f0) * c12;
-  weno7_si_sos(fm3, fm2, fm1, f0, fp1, fp2, fp3, si);
-  const float d[4] = {4.0f / 35.0f, 18.0f / 35.0f, 12.0f / 35.0f, 1.0f / 35.0f};
-  float w[4], ws = 0.0f, num = 0.0f;
-#pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const float t = si[r] + eps;
-    w[r] = __fdividef(d[r], t * t);
-    ws += w[r];
-    num += w[r] * f4[r];
-  }
-  return __fdividef(num, ws);
+  const float em3 = fm2 - fm3, em2 = fm1 - fm2, em1 = f0 - fm1;
+  const float e0 = fp1 - f0, e1 = fp2 - fp1, e2 = fp3 - fp2;
+  const float gm3 = em2 - em3, gm2 = em1 - em2, gm1 = e0 - em1, g0 = e1 - e0, g1 = e2 - e1;
+  const float hm3 = gm2 - gm3, hm2 = gm1 - gm2, hm1 = g0 - gm1, h0 = g1 - g0;
+  constexpr float s1 = 2.5819888974716112f;   // sqrt(20/3)
+  constexpr float s2 = 16.124515496597099f;   // sqrt(260)
+  constexpr float c3 = 781.0f / 3.0f;
+  const float a0 = s1 * (11.0f * e0 - 7.0f * e1 + 2.0f * e2);
+  const float a1 = s1 * (2.0f * em1 + 5.0f * e0 - e1);
+  const float a2 = s1 * (-em2 + 5.0f * em1 + 2.0f * e0);
+  const float a3 = s1 * (2.0f * em3 - 7.0f * em2 + 11.0f * em1);
+  const float b0 = s2 * (2.0f * g0 - g1);
+  const float b12 = s2 * gm1;
+  const float b3 = s2 * (2.0f * gm2 - gm3);
+  // SI_r + eps
+  const float t0 = fmaf(a0, a0, fmaf(b0, b0, fmaf(c3 * h0, h0, eps)));
+  const float t1 = fmaf(a1, a1, fmaf(b12, b12, fmaf(c3 * hm1, hm1, eps)));
+  const float t2 = fmaf(a2, a2, fmaf(b12, b12, fmaf(c3 * hm2, hm2, eps)));
+  const float t3 = fmaf(a3, a3, fmaf(b3, b3, fmaf(c3 * hm3, hm3, eps)));
+  const float d0 = 0.75f * e0 - (1.0f / 3.0f) * e1 + (1.0f / 12.0f) * e2;
+  const float d1 = (1.0f / 12.0f) * em1 + 0.5f * e0 - (1.0f / 12.0f) * e1;
+  const float d2 = -(1.0f / 12.0f) * em2 + (1.0f / 3.0f) * em1 + 0.25f * e0;
+  const float d3 = 0.25f * em3 - (5.0f / 6.0f) * em2 + (13.0f / 12.0f) * em1;
+  const float w0 = __fdividef(4.0f / 35.0f, t0 * t0);
+  const float w1 = __fdividef(18.0f / 35.0f, t1 * t1);
+  const float w2 = __fdividef(12.0f / 35.0f, t2 * t2);
+  const float w3 = __fdividef(1.0f / 35.0f, t3 * t3);
+  const float num = w0 * d0 + w1 * d1 + w2 * d2 + w3 * d3;
+  const float ws = (w0 + w1) + (w2 + w3);
+  return f0 + __fdividef(num, ws);
 }
 
 // ---------------------------------------------------------------- the kernel
