@@ -55,9 +55,14 @@ WORKLOAD = ("roofline run: nz=2^20, nv=256, z in [-25600,25600), dt=0.4 dz, mu=1
 #   kernel reads y, d1, d2, d3, d4 and writes y, y32.
 STAGE_BYTES = {"fp64": (16, 24, 24, 40, 0), "mixed": (8, 12, 12, 12, 36)}
 KERNEL_NAMES = ("stage 1", "stage 2", "stage 3", "stage 4", "increment")
-# Algorithmic FP64 flops per cell (4 reals) per launch of the fp64 stages
-# (moments, Hamiltonian, commutator, stencil, RK axpy; FMA = 2 flops).
-FP64_FLOPS_PER_CELL = {"fdko": (98, 106, 106, 138), "weno7": (482, 490, 490, 522)}
+# FP64 flops per cell (4 reals) per launch of the fp64 stages, counted from the
+# kernels' arithmetic (FMA = 2 flops, a division = 1): stage input y + delta 4
+# (stages 2-4), v-moment partials with the warp reduction 20 (FD4+KO, two
+# columns per thread) or 26 (WENO7, one), Hamiltonian 12, commutator 11,
+# advection 56 (FD4+KO: 14 per real) or 480 (WENO7: 116 per face for the
+# reconstruction in differences, 4 for the flux difference), output 4
+# (delta_s) or 32 (stage 4: the RK4 combination and y update).
+FP64_FLOPS_PER_CELL = {"fdko": (103, 107, 107, 135), "weno7": (533, 537, 537, 565)}
 SCHEMES = {"fdko": 0, "weno7": 1}
 PRECS = {"fp64": 0, "mixed": 1}
 # 152 SMs x 2 FP64 FMA lanes per clock x 2 flops x 2.07 GHz (nominal 1.25 TFLOP/s)

@@ -198,104 +198,106 @@ __device__ __forceinline__ int64_t wrap_row(int64_t r, int64_t nz) {
 // ---------------------------------------------------------------- WENO7 face
 // Value at i+1/2 of the 7th-order WENO reconstruction from the cell values
 // f_{i-3..i+3} (Appendix A: sub-stencil values Eq. (f4s), smoothness indices
-// Eq. (Si4) as printed, weights Eq. (weight) with linear weights 4/35, 18/35,
-// 12/35, 1/35 for S_0 = {i..i+3} .. S_3 = {i-3..i}).
-
-template <typename R>
-__device__ __forceinline__ void weno7_parts(R fm3, R fm2, R fm1, R f0, R fp1, R fp2, R fp3,
-                                            R (&f4)[4], R (&si)[4]) {
-  const R c12 = R(1) / R(12);
-  f4[0] = (R(3) * f0 + R(13) * fp1 - R(5) * fp2 + fp3) * c12;
-  f4[1] = (-fm1 + R(7) * f0 + R(7) * fp1 - fp2) * c12;
-  f4[2] = (fm2 - R(5) * fm1 + R(13) * f0 + R(3) * fp1) * c12;
-  f4[3] = (R(-3) * fm3 + R(13) * fm2 - R(23) * fm1 + R(25) * f0) * c12;
-  si[0] = f0 * (R(2107) * f0 - R(9402) * fp1 + R(7042) * fp2 - R(1854) * fp3) +
-          fp1 * (R(11003) * fp1 - R(17246) * fp2 + R(4642) * fp3) +
-          fp2 * (R(7043) * fp2 - R(3882) * fp3) + R(547) * fp3 * fp3;
-  si[1] = fm1 * (R(547) * fm1 - R(2522) * f0 + R(1922) * fp1 - R(494) * fp2) +
-          f0 * (R(3443) * f0 - R(5966) * fp1 + R(1602) * fp2) +
-          fp1 * (R(2843) * fp1 - R(1642) * fp2) + R(267) * fp2 * fp2;
-  si[2] = fm2 * (R(267) * fm2 - R(1642) * fm1 + R(1602) * f0 - R(494) * fp1) +
-          fm1 * (R(2843) * fm1 - R(5966) * f0 + R(1922) * fp1) +
-          f0 * (R(3443) * f0 - R(2522) * fp1) + R(547) * fp1 * fp1;
-  si[3] = fm3 * (R(547) * fm3 - R(3882) * fm2 + R(4642) * fm1 - R(1854) * f0) +
-          fm2 * (R(7043) * fm2 - R(17246) * fm1 + R(7042) * f0) +
-          fm1 * (R(11003) * fm1 - R(9402) * f0) + R(2107) * f0 * f0;
-}
+// Eq. (Si4), weights Eq. (weight) with linear weights d = 4/35, 18/35, 12/35,
+// 1/35 for S_0 = {i..i+3} .. S_3 = {i-3..i}), written in the first, second and
+// third differences of the seven values,
+//   e_k = f_{k+1} - f_k (k = -3..2), g_k = e_{k+1} - e_k, h_k = g_{k+1} - g_k.
+// Candidate values: f4_r = f_0 + delta_r with
+//   delta_0 = 3/4 e_0 - 1/3 e_1 + 1/12 e_2     delta_1 = 1/12 e_-1 + 1/2 e_0 - 1/12 e_1
+//   delta_2 = -1/12 e_-2 + 1/3 e_-1 + 1/4 e_0  delta_3 = 1/4 e_-3 - 5/6 e_-2 + 13/12 e_-1.
+// Smoothness indicators as sums of squares: SI_r is 240 times the Jiang-Shu
+// integral of the squared first three derivatives of the sub-stencil's cubic,
+// which in these differences reads
+//   SI_r = (20/3) a_r^2 + 260 b_r^2 + (781/3) c_r^2,
+//   a = (11 e_0 - 7 e_1 + 2 e_2, 2 e_-1 + 5 e_0 - e_1, -e_-2 + 5 e_-1 + 2 e_0,
+//        2 e_-3 - 7 e_-2 + 11 e_-1)           (6 x the cubic's slope at f_0's face)
+//   b = (2 g_0 - g_1, g_-1, g_-1, 2 g_-2 - g_-3),  c = (h_0, h_-1, h_-2, h_-3)
+// (exact rational identities with the printed forms).  The printed quadratic
+// forms have coefficients up to 1.7e4: in float they lose ~1e-3 to cancellation
+// for values of order one, enough to turn an indicator negative and bring
+// SI + eps to zero, while the squares keep every indicator >= 0 to full
+// precision.  The difference form also takes about a quarter fewer operations.
+// The square roots of 20/3 and 260 are folded into the coefficients of a and b,
+// the linear weights into those of delta_r.
 
 // double: one division per face.  With q_r = (SI_r + eps)^2 the normalised
 // weights d_r / q_r / sum_k (d_k / q_k) equal d_r prod_{k!=r} q_k /
 // sum_j d_j prod_{k!=j} q_k (q_r >= eps^2 keeps the products in range).
 __device__ __forceinline__ double weno7_face(double fm3, double fm2, double fm1, double f0,
                                              double fp1, double fp2, double fp3, double eps) {
-  double f4[4], si[4];
-  weno7_parts(fm3, fm2, fm1, f0, fp1, fp2, fp3, f4, si);
-  double q[4];
-#pragma unroll
-  for (int r = 0; r < 4; ++r) {
-    const double t = si[r] + eps;
-    q[r] = t * t;
-  }
-  const double q01 = q[0] * q[1], q23 = q[2] * q[3];
-  const double a0 = (4.0 / 35.0) * (q[1] * q23);
-  const double a1 = (18.0 / 35.0) * (q[0] * q23);
-  const double a2 = (12.0 / 35.0) * (q01 * q[3]);
-  const double a3 = (1.0 / 35.0) * (q01 * q[2]);
-  const double num = a0 * f4[0] + a1 * f4[1] + a2 * f4[2] + a3 * f4[3];
-  return num / (a0 + a1 + a2 + a3);
+  const double em3 = fm2 - fm3, em2 = fm1 - fm2, em1 = f0 - fm1;
+  const double e0 = fp1 - f0, e1 = fp2 - fp1, e2 = fp3 - fp2;
+  const double gm3 = em2 - em3, gm2 = em1 - em2, gm1 = e0 - em1, g0 = e1 - e0, g1 = e2 - e1;
+  const double hm3 = gm2 - gm3, hm2 = gm1 - gm2, hm1 = g0 - gm1, h0 = g1 - g0;
+  constexpr double s1 = 2.5819888974716112;  // sqrt(20/3)
+  constexpr double s2 = 16.124515496597099;  // sqrt(260)
+  constexpr double c3 = 781.0 / 3.0;
+  const double a0 = (11.0 * s1) * e0 - (7.0 * s1) * e1 + (2.0 * s1) * e2;
+  const double a1 = (2.0 * s1) * em1 + (5.0 * s1) * e0 - s1 * e1;
+  const double a2 = -s1 * em2 + (5.0 * s1) * em1 + (2.0 * s1) * e0;
+  const double a3 = (2.0 * s1) * em3 - (7.0 * s1) * em2 + (11.0 * s1) * em1;
+  const double b0 = (2.0 * s2) * g0 - s2 * g1;
+  const double b12 = s2 * gm1;
+  const double b3 = (2.0 * s2) * gm2 - s2 * gm3;
+  const double t0 = fma(a0, a0, fma(b0, b0, fma(c3 * h0, h0, eps)));
+  const double t1 = fma(a1, a1, fma(b12, b12, fma(c3 * hm1, hm1, eps)));
+  const double t2 = fma(a2, a2, fma(b12, b12, fma(c3 * hm2, hm2, eps)));
+  const double t3 = fma(a3, a3, fma(b3, b3, fma(c3 * hm3, hm3, eps)));
+  const double dd0 = (3.0 / 35.0) * e0 - (4.0 / 105.0) * e1 + (1.0 / 105.0) * e2;
+  const double dd1 = (3.0 / 70.0) * em1 + (9.0 / 35.0) * e0 - (3.0 / 70.0) * e1;
+  const double dd2 = -(1.0 / 35.0) * em2 + (4.0 / 35.0) * em1 + (3.0 / 35.0) * e0;
+  const double dd3 = (1.0 / 140.0) * em3 - (1.0 / 42.0) * em2 + (13.0 / 420.0) * em1;
+  const double q0 = t0 * t0, q1 = t1 * t1, q2 = t2 * t2, q3 = t3 * t3;
+  const double q01 = q0 * q1, q23 = q2 * q3;
+  const double p0 = q1 * q23, p1 = q0 * q23, p2 = q01 * q3, p3 = q01 * q2;
+  const double num = p0 * dd0 + p1 * dd1 + p2 * dd2 + p3 * dd3;
+  const double den = (4.0 / 35.0) * p0 + (18.0 / 35.0) * p1 + (12.0 / 35.0) * p2 + (1.0 / 35.0) * p3;
+  return f0 + num / den;
 }
 
-// float: the same reconstruction written in the first, second and third
-// differences of the seven values,
-//   e_k = f_{k+1} - f_k (k = -3..2), g_k = e_{k+1} - e_k, h_k = g_{k+1} - g_k.
-// Candidate values (Eq. (f4s)): f4_r = f_0 + delta_r with
-//   delta_0 = 3/4 e_0 - 1/3 e_1 + 1/12 e_2     delta_1 = 1/12 e_-1 + 1/2 e_0 - 1/12 e_1
-//   delta_2 = -1/12 e_-2 + 1/3 e_-1 + 1/4 e_0  delta_3 = 1/4 e_-3 - 5/6 e_-2 + 13/12 e_-1.
-// Smoothness indicators (Eq. (Si4)) as sums of squares: SI_r is 240 times the
-// Jiang-Shu integral of the squared first three derivatives of the sub-stencil's
-// cubic, which in these differences reads
-//   SI_r = (20/3) a_r^2 + 260 b_r^2 + (781/3) c_r^2,
-//   a = (11 e_0 - 7 e_1 + 2 e_2, 2 e_-1 + 5 e_0 - e_1, -e_-2 + 5 e_-1 + 2 e_0,
-//        2 e_-3 - 7 e_-2 + 11 e_-1)           (6 x the cubic's slope at f_0's face)
-//   b = (2 g_0 - g_1, g_-1, g_-1, 2 g_-2 - g_-3),  c = (h_0, h_-1, h_-2, h_-3)
-// (exact rational identities with the printed forms).  In float the printed
-// forms lose ~1e-3 (coefficients up to 1.7e4 times values of order one) to
-// cancellation, enough to turn an indicator negative and bring SI + eps to
-// zero; the squares keep every indicator >= 0 to full precision, and the
-// differences make the reconstruction about a quarter cheaper.  The square
-// roots of 20/3 and 260 are folded into the coefficients of a and b.
-// Weights Eq. (weight) with fast reciprocals (the mixed path's weights need no more).
+// Approximate reciprocal (the special-function unit's, relative error ~2^-23;
+// inputs here are >= eps^2, normal floats).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// float: fast reciprocals for the weights (the mixed path's weights need no more).
 __device__ __forceinline__ float weno7_face(float fm3, float fm2, float fm1, float f0, float fp1,
                                             float fp2, float fp3, float eps) {
   const float em3 = fm2 - fm3, em2 = fm1 - fm2, em1 = f0 - fm1;
   const float e0 = fp1 - f0, e1 = fp2 - fp1, e2 = fp3 - fp2;
   const float gm3 = em2 - em3, gm2 = em1 - em2, gm1 = e0 - em1, g0 = e1 - e0, g1 = e2 - e1;
   const float hm3 = gm2 - gm3, hm2 = gm1 - gm2, hm1 = g0 - gm1, h0 = g1 - g0;
-  constexpr float s1 = 2.5819888974716112f;   // sqrt(20/3)
-  constexpr float s2 = 16.124515496597099f;   // sqrt(260)
+  constexpr float s1 = 2.5819888974716112f;  // sqrt(20/3)
+  constexpr float s2 = 16.124515496597099f;  // sqrt(260)
   constexpr float c3 = 781.0f / 3.0f;
-  const float a0 = s1 * (11.0f * e0 - 7.0f * e1 + 2.0f * e2);
-  const float a1 = s1 * (2.0f * em1 + 5.0f * e0 - e1);
-  const float a2 = s1 * (-em2 + 5.0f * em1 + 2.0f * e0);
-  const float a3 = s1 * (2.0f * em3 - 7.0f * em2 + 11.0f * em1);
-  const float b0 = s2 * (2.0f * g0 - g1);
+  // sqrt(20/3) a_r and sqrt(260) b_r
+  const float a0 = (11.0f * s1) * e0 - (7.0f * s1) * e1 + (2.0f * s1) * e2;
+  const float a1 = (2.0f * s1) * em1 + (5.0f * s1) * e0 - s1 * e1;
+  const float a2 = -s1 * em2 + (5.0f * s1) * em1 + (2.0f * s1) * e0;
+  const float a3 = (2.0f * s1) * em3 - (7.0f * s1) * em2 + (11.0f * s1) * em1;
+  const float b0 = (2.0f * s2) * g0 - s2 * g1;
   const float b12 = s2 * gm1;
-  const float b3 = s2 * (2.0f * gm2 - gm3);
+  const float b3 = (2.0f * s2) * gm2 - s2 * gm3;
   // SI_r + eps
   const float t0 = fmaf(a0, a0, fmaf(b0, b0, fmaf(c3 * h0, h0, eps)));
   const float t1 = fmaf(a1, a1, fmaf(b12, b12, fmaf(c3 * hm1, hm1, eps)));
   const float t2 = fmaf(a2, a2, fmaf(b12, b12, fmaf(c3 * hm2, hm2, eps)));
   const float t3 = fmaf(a3, a3, fmaf(b3, b3, fmaf(c3 * hm3, hm3, eps)));
-  const float d0 = 0.75f * e0 - (1.0f / 3.0f) * e1 + (1.0f / 12.0f) * e2;
-  const float d1 = (1.0f / 12.0f) * em1 + 0.5f * e0 - (1.0f / 12.0f) * e1;
-  const float d2 = -(1.0f / 12.0f) * em2 + (1.0f / 3.0f) * em1 + 0.25f * e0;
-  const float d3 = 0.25f * em3 - (5.0f / 6.0f) * em2 + (13.0f / 12.0f) * em1;
-  const float w0 = __fdividef(4.0f / 35.0f, t0 * t0);
-  const float w1 = __fdividef(18.0f / 35.0f, t1 * t1);
-  const float w2 = __fdividef(12.0f / 35.0f, t2 * t2);
-  const float w3 = __fdividef(1.0f / 35.0f, t3 * t3);
-  const float num = w0 * d0 + w1 * d1 + w2 * d2 + w3 * d3;
-  const float ws = (w0 + w1) + (w2 + w3);
+  // d_r delta_r: the linear weights 4/35, 18/35, 12/35, 1/35 folded into the
+  // candidates' coefficients
+  const float dd0 = (3.0f / 35.0f) * e0 - (4.0f / 105.0f) * e1 + (1.0f / 105.0f) * e2;
+  const float dd1 = (3.0f / 70.0f) * em1 + (9.0f / 35.0f) * e0 - (3.0f / 70.0f) * e1;
+  const float dd2 = -(1.0f / 35.0f) * em2 + (4.0f / 35.0f) * em1 + (3.0f / 35.0f) * e0;
+  const float dd3 = (1.0f / 140.0f) * em3 - (1.0f / 42.0f) * em2 + (13.0f / 420.0f) * em1;
+  // 1 / (SI_r + eps)^2; the nonlinear weights are d_r times these
+  const float q0 = rcp_approx(t0 * t0), q1 = rcp_approx(t1 * t1);
+  const float q2 = rcp_approx(t2 * t2), q3 = rcp_approx(t3 * t3);
+  const float num = q0 * dd0 + q1 * dd1 + q2 * dd2 + q3 * dd3;
+  const float ws = (4.0f / 35.0f) * q0 + (18.0f / 35.0f) * q1 + (12.0f / 35.0f) * q2 +
+                   (1.0f / 35.0f) * q3;
   return f0 + __fdividef(num, ws);
 }
 

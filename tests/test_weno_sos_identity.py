@@ -1,7 +1,8 @@
-"""The float WENO7 path evaluates the smoothness indicators of Eq. (Si4) as sums
-of squares, and both the indicators and the candidate values of Eq. (f4s) in the
-first, second and third differences of the seven cell values (stage_kernel.cuh,
-the float weno7_face).  Those forms must equal the printed ones exactly; checked
+"""The WENO7 kernels (both precisions) evaluate the smoothness indicators of
+Eq. (Si4) as sums of squares, and both the indicators and the candidate values of
+Eq. (f4s) in the first, second and third differences of the seven cell values,
+with the linear weights folded into the candidates' coefficients
+(stage_kernel.cuh, weno7_face).  Those forms must equal the printed ones exactly; checked
 here in exact rational arithmetic on random integer data and on the basis
 vectors (which fixes every coefficient of the linear and quadratic forms)."""
 from fractions import Fraction as F
@@ -74,7 +75,11 @@ def difference_form(f):
              F(1, 12) * em1 + F(1, 2) * e0 - F(1, 12) * e1,
              -F(1, 12) * em2 + F(1, 3) * em1 + F(1, 4) * e0,
              F(1, 4) * em3 - F(5, 6) * em2 + F(13, 12) * em1]
-    return [f0 + d for d in delta], si
+    dd = [F(3, 35) * e0 - F(4, 105) * e1 + F(1, 105) * e2,
+          F(3, 70) * em1 + F(9, 35) * e0 - F(3, 70) * e1,
+          -F(1, 35) * em2 + F(4, 35) * em1 + F(3, 35) * e0,
+          F(1, 140) * em3 - F(1, 42) * em2 + F(13, 420) * em1]
+    return [f0 + d for d in delta], si, dd
 
 
 def _cases():
@@ -91,15 +96,18 @@ def _cases():
 
 def test_difference_form_equals_printed_forms():
     for f in _cases():
-        cand, si = difference_form(f)
+        cand, si, dd = difference_form(f)
         assert cand == printed_candidates(f)
         assert si == printed(f)
+        # linear weights of Eq. (weight) folded into the candidates
+        d = [F(4, 35), F(18, 35), F(12, 35), F(1, 35)]
+        assert dd == [d[r] * (cand[r] - f[3]) for r in range(4)]
 
 
 def test_difference_form_catches_a_wrong_coefficient():
     # the check above is not vacuous: one coefficient off by one is detected
     f = [F(x) for x in (3, -1, 4, 1, -5, 9, 2)]
-    cand, si = difference_form(f)
+    cand, si, dd = difference_form(f)
     fm3, fm2, fm1, f0, fp1, fp2, fp3 = f
     em2, em1, e0 = fm1 - fm2, f0 - fm1, fp1 - f0
     wrong = -F(1, 12) * em2 + F(1, 3) * em1 + F(1, 3) * e0 + f0
