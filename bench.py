@@ -59,10 +59,11 @@ KERNEL_NAMES = ("stage 1", "stage 2", "stage 3", "stage 4", "increment")
 # kernels' arithmetic (FMA = 2 flops, a division = 1): stage input y + delta 4
 # (stages 2-4), v-moment partials with the warp reduction 20 (FD4+KO, two
 # columns per thread) or 26 (WENO7, one), Hamiltonian 12, commutator 11,
-# advection 56 (FD4+KO: 14 per real) or 480 (WENO7: 116 per face for the
-# reconstruction in differences, 4 for the flux difference), output 4
-# (delta_s) or 32 (stage 4: the RK4 combination and y update).
-FP64_FLOPS_PER_CELL = {"fdko": (103, 107, 107, 135), "weno7": (533, 537, 537, 565)}
+# advection 40 (FD4+KO: one FMA per window row, the two stencils combined) or
+# 480 (WENO7: 116 per face for the reconstruction in differences, 4 for the
+# flux difference), output 4 (delta_s) or 32 (stage 4: the RK4 combination and
+# y update).
+FP64_FLOPS_PER_CELL = {"fdko": (87, 91, 91, 119), "weno7": (533, 537, 537, 565)}
 SCHEMES = {"fdko": 0, "weno7": 1}
 PRECS = {"fp64": 0, "mixed": 1}
 # 152 SMs x 2 FP64 FMA lanes per clock x 2 flops x 2.07 GHz (nominal 1.25 TFLOP/s)
