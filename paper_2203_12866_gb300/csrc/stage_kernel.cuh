@@ -264,15 +264,14 @@ __device__ __forceinline__ float rcp_approx(float x) {
 }
 
 // float: fast reciprocals for the weights (the mixed path's weights need no more).
-__device__ __forceinline__ float weno7_face(float fm3, float fm2, float fm1, float f0, float fp1,
-                                            float fp2, float fp3, float eps) {
-  const float em3 = fm2 - fm3, em2 = fm1 - fm2, em1 = f0 - fm1;
-  const float e0 = fp1 - f0, e1 = fp2 - fp1, e2 = fp3 - fp2;
-  const float gm3 = em2 - em3, gm2 = em1 - em2, gm1 = e0 - em1, g0 = e1 - e0, g1 = e2 - e1;
-  const float hm3 = gm2 - gm3, hm2 = gm1 - gm2, hm1 = g0 - gm1, h0 = g1 - g0;
+// The face from its differences e_-3..e_2, g_-3..g_1 and the third-difference
+// terms T_r = (781/3) c_r^2 + eps (T_0 from h_0 .. T_3 from h_-3).
+__device__ __forceinline__ float weno7_face_core(float f0, float em3, float em2, float em1,
+                                                 float e0, float e1, float e2, float gm3,
+                                                 float gm2, float gm1, float g0, float g1,
+                                                 float T0, float T1, float T2, float T3) {
   constexpr float s1 = 2.5819888974716112f;  // sqrt(20/3)
   constexpr float s2 = 16.124515496597099f;  // sqrt(260)
-  constexpr float c3 = 781.0f / 3.0f;
   // sqrt(20/3) a_r and sqrt(260) b_r
   const float a0 = (11.0f * s1) * e0 - (7.0f * s1) * e1 + (2.0f * s1) * e2;
   const float a1 = (2.0f * s1) * em1 + (5.0f * s1) * e0 - s1 * e1;
@@ -282,10 +281,10 @@ __device__ __forceinline__ float weno7_face(float fm3, float fm2, float fm1, flo
   const float b12 = s2 * gm1;
   const float b3 = (2.0f * s2) * gm2 - s2 * gm3;
   // SI_r + eps
-  const float t0 = fmaf(a0, a0, fmaf(b0, b0, fmaf(c3 * h0, h0, eps)));
-  const float t1 = fmaf(a1, a1, fmaf(b12, b12, fmaf(c3 * hm1, hm1, eps)));
-  const float t2 = fmaf(a2, a2, fmaf(b12, b12, fmaf(c3 * hm2, hm2, eps)));
-  const float t3 = fmaf(a3, a3, fmaf(b3, b3, fmaf(c3 * hm3, hm3, eps)));
+  const float t0 = fmaf(a0, a0, fmaf(b0, b0, T0));
+  const float t1 = fmaf(a1, a1, fmaf(b12, b12, T1));
+  const float t2 = fmaf(a2, a2, fmaf(b12, b12, T2));
+  const float t3 = fmaf(a3, a3, fmaf(b3, b3, T3));
   // d_r delta_r: the linear weights 4/35, 18/35, 12/35, 1/35 folded into the
   // candidates' coefficients
   const float dd0 = (3.0f / 35.0f) * e0 - (4.0f / 105.0f) * e1 + (1.0f / 105.0f) * e2;
@@ -299,6 +298,38 @@ __device__ __forceinline__ float weno7_face(float fm3, float fm2, float fm1, flo
   const float ws = (4.0f / 35.0f) * q0 + (18.0f / 35.0f) * q1 + (12.0f / 35.0f) * q2 +
                    (1.0f / 35.0f) * q3;
   return f0 + __fdividef(num, ws);
+}
+
+// The value unchanged, opaque to the optimiser: keeps two evaluations of
+// weno7_face_core from sharing products (whose fused multiply-adds would then
+// round differently), so a face is bitwise the same whichever of the pair it is.
+__device__ __forceinline__ float opaque(float x) {
+  asm volatile("" : "+f"(x));
+  return x;
+}
+
+// Two adjacent float faces from eight values x_0..x_7: P from x_0..x_6 (f_0 =
+// x_3) and Q from x_1..x_7 (f_0 = x_4).  The differences and the third-difference
+// terms of the overlapping stencils are formed once.
+__device__ __forceinline__ void weno7_face_pair(float x0, float x1, float x2, float x3, float x4,
+                                                float x5, float x6, float x7, float eps,
+                                                float& P, float& Q) {
+  constexpr float c3 = 781.0f / 3.0f;
+  const float e0 = x1 - x0, e1 = x2 - x1, e2 = x3 - x2, e3 = x4 - x3, e4 = x5 - x4,
+              e5 = x6 - x5, e6 = x7 - x6;
+  const float g0 = e1 - e0, g1 = e2 - e1, g2 = e3 - e2, g3 = e4 - e3, g4 = e5 - e4, g5 = e6 - e5;
+  const float h0 = g1 - g0, h1 = g2 - g1, h2 = g3 - g2, h3 = g4 - g3, h4 = g5 - g4;
+  const float T0 = fmaf(c3 * h0, h0, eps), T1 = fmaf(c3 * h1, h1, eps),
+              T2 = fmaf(c3 * h2, h2, eps), T3 = fmaf(c3 * h3, h3, eps),
+              T4 = fmaf(c3 * h4, h4, eps);
+  // local indices: e_-3 .. e_2 = e[b] .. e[b+5], g_-3 .. g_1 = g[b] .. g[b+4],
+  // h_-3 .. h_0 = h[b] .. h[b+3] for the stencil starting at x_b
+  P = weno7_face_core(opaque(x3), opaque(e0), opaque(e1), opaque(e2), opaque(e3), opaque(e4),
+                      opaque(e5), opaque(g0), opaque(g1), opaque(g2), opaque(g3), opaque(g4),
+                      opaque(T3), opaque(T2), opaque(T1), opaque(T0));
+  Q = weno7_face_core(opaque(x4), opaque(e1), opaque(e2), opaque(e3), opaque(e4), opaque(e5),
+                      opaque(e6), opaque(g1), opaque(g2), opaque(g3), opaque(g4), opaque(g5),
+                      opaque(T4), opaque(T3), opaque(T2), opaque(T1));
 }
 
 // ---------------------------------------------------------------- the kernel

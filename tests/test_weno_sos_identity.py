@@ -2,7 +2,8 @@
 Eq. (Si4) as sums of squares, and both the indicators and the candidate values of
 Eq. (f4s) in the first, second and third differences of the seven cell values,
 with the linear weights folded into the candidates' coefficients
-(stage_kernel.cuh, weno7_face).  Those forms must equal the printed ones exactly; checked
+(stage_kernel.cuh: weno7_face for FP64, weno7_face_core / weno7_face_pair
+for float).  Those forms must equal the printed ones exactly; checked
 here in exact rational arithmetic on random integer data and on the basis
 vectors (which fixes every coefficient of the linear and quadratic forms)."""
 from fractions import Fraction as F
