@@ -134,7 +134,8 @@ class ClockSampler:
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("stage_kernel.cuh", "stage_body.inc", "cosenu_device.cuh"):
+    for f in ("stage_kernel.cuh", "stage_body.inc", "cosenu_device.cuh", "diag_kernels.cu",
+              "diag_kernels.cuh"):
         h.update(open(os.path.join(ROOT, "paper_2203_12866_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
