@@ -220,7 +220,9 @@ int cosenu_spectrum(cosenu_t h, int32_t species, int32_t v_index, int64_t m0, in
  * directly rather than replayed from a graph).  cosenu_stage_times waits for
  * the stream and returns, per kernel k of an RK4 step (k = 1..4: the fused
  * stage kernels; k = 5: the mixed path's state-increment kernel, zero launches
- * in the FP64 path), the summed device time in milliseconds ms[k-1] and the
+ * in the FP64 path; the small kernel after it that folds the increment's
+ * v-moments into the running moments of y is not timed), the summed device
+ * time in milliseconds ms[k-1] and the
  * number of timed launches n[k-1] since the last call (arrays of 5; either
  * pointer may be NULL), then clears the sums. */
 int cosenu_set_stage_timing(cosenu_t h, int on);

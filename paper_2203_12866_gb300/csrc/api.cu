@@ -56,8 +56,10 @@ Layout make_layout(int64_t nz, int32_t nv, int precision) {
   const size_t n4 = precision == COSENU_MIXED ? n : 0;  // delta_4 (mixed)
   L.d4 = off; off = align_up(off + n4 * dsz);
   L.my = off; off = align_up(off + (size_t)nz * 8 * sizeof(double));
-  const size_t nmd = precision == COSENU_MIXED ? (size_t)2 * nz * 8 : 0;
-  L.mdel = off; off = align_up(off + nmd * sizeof(float));
+  const size_t npm = precision == COSENU_MIXED ? (size_t)8 * nz : 0;
+  L.pmom = off; off = align_up(off + npm * sizeof(float2));
+  const size_t nwt = precision == COSENU_MIXED ? (size_t)2 * nv : 0;
+  L.wtab = off; off = align_up(off + nwt * sizeof(float));
   L.zavg = off; off = align_up(off + (size_t)8 * nv * sizeof(double));
   L.vtab = off; off = align_up(off + (size_t)2 * nv * sizeof(double));
   L.partial = off; off = align_up(off + (size_t)kDiagMaxBlocks * 8 * sizeof(double));
@@ -196,7 +198,7 @@ int slot_bytes_of(int precision, int nv, int stage, int rows) {
 // missing buffer is refused instead of faulting on the device).
 bool stage_args_complete(int precision, int stage, const StageArgs& a) {
   const bool mixed = precision == COSENU_MIXED;
-  if (!a.err || !a.vtab || (mixed ? !a.y32_in || !a.my || !a.mdel : !a.y_in)) return false;
+  if (!a.err || !a.vtab || (mixed ? !a.y32_in || !a.my : !a.y_in)) return false;
   if (stage > 1 && !a.d_in) return false;
   if ((stage < 4 || mixed) && !a.d_out) return false;
   if (stage == 4 && !mixed && (!a.d1 || !a.d2 || !a.y_out)) return false;
@@ -291,7 +293,6 @@ StageArgs stage_args(const cosenu_s* h, int stage, int ycur) {
   a.y_out = h->y[ycur ^ 1];
   a.y32_in = h->y32[0];
   a.my = h->my;
-  a.mdel = h->mdel;
   a.err = h->err;
   switch (stage) {
     case 1: a.d_out = h->d[0]; break;
@@ -301,6 +302,23 @@ StageArgs stage_args(const cosenu_s* h, int stage, int ycur) {
       a.d_in = h->d[2]; a.d1 = h->d[0]; a.d2 = h->d[1]; a.d_out = h->d[3]; break;
   }
   return a;
+}
+
+// The mixed path's increment kernels of one handle.
+ApplySeg apply_seg(const cosenu_s* h) {
+  ApplySeg sg;
+  sg.y = h->y[0];
+  sg.y32 = h->y32[0];
+  for (int k = 0; k < 4; ++k) sg.d[k] = static_cast<const float*>(h->d[k]);
+  sg.pmom = h->pmom;
+  sg.wtab = h->wtab;
+  sg.my = h->my;
+  sg.nz = h->nz;
+  sg.nv = h->nv;
+  sg.rows_per_chunk = apply_rows_per_chunk(h->nv);
+  sg.nchunks = (8 * h->nz + sg.rows_per_chunk - 1) / sg.rows_per_chunk;
+  sg.err = h->err;
+  return sg;
 }
 
 }  // namespace cosenu
@@ -316,22 +334,34 @@ cudaError_t take_event(cosenu_t h, cudaEvent_t* out) {
   return cudaEventCreate(out);
 }
 
-cudaError_t launch_apply(cosenu_t h) {
-  const int64_t n = 8 * h->nz * (int64_t)h->nv;
-  const int64_t blocks = std::min<int64_t>((n / 4 + 255) / 256, (int64_t)h->nsm * 8);
-  apply_increment_kernel<<<(int)blocks, 256, 0, h->stream>>>(
-      h->y[0], h->y32[0], static_cast<const float*>(h->d[0]), static_cast<const float*>(h->d[1]),
-      static_cast<const float*>(h->d[2]), static_cast<const float*>(h->d[3]), n, h->err);
+
+// End of a mixed RK4 step: y <- y + dy with the plane-row v-sums of dy
+// (kernel 5), then the running FP64 moments of y advanced by them (kernel 6).
+cudaError_t launch_apply(cosenu_t h, int k) {
+  if (k == 5) {
+    const ApplySeg sg = apply_seg(h);
+    const int64_t blocks = std::min<int64_t>(sg.nchunks, (int64_t)h->nsm * 8);
+    apply_increment_kernel<<<(int)blocks, kApplyThreads, 0, h->stream>>>(sg);
+  } else {
+    const int64_t blocks = std::min<int64_t>((h->nz + 255) / 256, (int64_t)h->nsm * 8);
+    fold_moments_kernel<<<(int)blocks, 256, 0, h->stream>>>(h->my, h->pmom, h->nz);
+  }
   cudaError_t e = cudaGetLastError();
   if (e == cudaSuccess) g_launches.fetch_add(1, std::memory_order_relaxed);
   return e;
 }
 
-// One RK4 step: stages 1-4, then (mixed) the increment kernel.  Kernel k of the
-// step (1..4 stages, 5 increment) is bracketed by events when timing is on.
+// One RK4 step: stages 1-4, then (mixed) the increment kernel and the moment
+// fold.  Kernels 1..5 of the step (stages, increment) are bracketed by events
+// when timing is on; the fold (a few hundredths of a millisecond) is not.
 cudaError_t enqueue_step(cosenu_t h, int ycur) {
-  const int nk = h->precision == COSENU_MIXED ? 5 : 4;
+  const int nk = h->precision == COSENU_MIXED ? 6 : 4;
   for (int s = 1; s <= nk; ++s) {
+    if (s == 6) {
+      cudaError_t e = launch_apply(h, 6);
+      if (e != cudaSuccess) return e;
+      continue;
+    }
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (h->timing) {
       cudaError_t e = take_event(h, &e0);
@@ -339,7 +369,7 @@ cudaError_t enqueue_step(cosenu_t h, int ycur) {
       if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
       if (e != cudaSuccess) return e;
     }
-    cudaError_t e = s <= 4 ? launch_stage(h, s, stage_args(h, s, ycur)) : launch_apply(h);
+    cudaError_t e = s <= 4 ? launch_stage(h, s, stage_args(h, s, ycur)) : launch_apply(h, 5);
     if (e != cudaSuccess) return e;
     if (h->timing) {
       e = cudaEventRecord(e1, h->stream);
@@ -393,13 +423,19 @@ void default_params(cosenu_t h) {
 // table (the stage kernels read them once per column).
 cudaError_t upload_vtab(cosenu_t h) {
   std::vector<double> t((size_t)2 * h->nv);
+  std::vector<float> w((size_t)2 * h->nv);  // mixed: w_j and w_j v_j rounded to float
   for (int j = 0; j < h->nv; ++j) {
     t[j] = vgrid_v(j, h->nv, h->vgrid);
     t[(size_t)h->nv + j] = vgrid_w(j, h->nv, h->vgrid);
+    w[j] = (float)t[(size_t)h->nv + j];
+    w[(size_t)h->nv + j] = (float)(t[(size_t)h->nv + j] * t[j]);
   }
   cudaError_t e = cudaMemcpyAsync(h->vtab, t.data(), t.size() * sizeof(double),
                                   cudaMemcpyHostToDevice, h->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // t dies here
+  if (e == cudaSuccess && h->wtab)
+    e = cudaMemcpyAsync(h->wtab, w.data(), w.size() * sizeof(float), cudaMemcpyHostToDevice,
+                        h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);  // t, w die here
   return e;
 }
 
@@ -462,7 +498,8 @@ cosenu_t create_common(int64_t nz, int32_t nv, double L, int scheme, int precisi
   h->d[2] = h->ws + h->lay.d3;
   if (precision == COSENU_MIXED) {
     h->d[3] = h->ws + h->lay.d4;
-    h->mdel = reinterpret_cast<float*>(h->ws + h->lay.mdel);
+    h->pmom = reinterpret_cast<float2*>(h->ws + h->lay.pmom);
+    h->wtab = reinterpret_cast<float*>(h->ws + h->lay.wtab);
   }
   h->my = reinterpret_cast<double*>(h->ws + h->lay.my);
   h->err = reinterpret_cast<uint32_t*>(h->ws + h->lay.err);

@@ -60,9 +60,9 @@ struct ClassPlan {
   StageCfg cfg[5];
   int occ[5] = {};
   size_t inst_off[5][2] = {}, item_off[5] = {};
-  size_t seg_off = 0, chunk_off = 0;
+  size_t seg_off = 0, chunk_off = 0, fold_off = 0;
   int nseg = 0;
-  int64_t nchunks = 0;
+  int64_t nchunks = 0, nfold = 0;  // increment chunks, fold blocks
   double kernel_ms[6] = {};  // mean device time per launch at the last cosenu_batch_stage_times
 };
 
@@ -205,25 +205,24 @@ int write_tables(cosenu_batch_t b) {
     }
     c.nseg = 0;
     c.nchunks = 0;
+    c.nfold = 0;
     if (c.key.precision == COSENU_MIXED) {
       std::vector<ApplySeg> segs;
-      std::vector<int64_t> chunk_first;
+      std::vector<int64_t> chunk_first, fold_first;
       for (int mi : c.members) {
-        const cosenu_t h = b->members[mi];
-        ApplySeg sg;
-        sg.y = h->y[0];
-        sg.y32 = h->y32[0];
-        for (int k = 0; k < 4; ++k) sg.d[k] = static_cast<const float*>(h->d[k]);
-        sg.n4 = 2 * h->nz * (int64_t)h->nv;
-        sg.err = h->err;
+        const ApplySeg sg = apply_seg(b->members[mi]);
         segs.push_back(sg);
         chunk_first.push_back(c.nchunks);
-        c.nchunks += (sg.n4 + kApplyChunk4 - 1) / kApplyChunk4;
+        c.nchunks += sg.nchunks;
+        fold_first.push_back(c.nfold);
+        c.nfold += (sg.nz + kFoldRows - 1) / kFoldRows;
       }
       chunk_first.push_back(c.nchunks);
+      fold_first.push_back(c.nfold);
       c.nseg = (int)segs.size();
       c.seg_off = img.put(segs.data(), segs.size() * sizeof(ApplySeg));
       c.chunk_off = img.put(chunk_first.data(), chunk_first.size() * sizeof(int64_t));
+      c.fold_off = img.put(fold_first.data(), fold_first.size() * sizeof(int64_t));
     }
   }
   // error flags: every member's word
@@ -313,14 +312,23 @@ cudaError_t take_event(cosenu_batch_t b, cudaEvent_t* out) {
   return cudaEventCreate(out);
 }
 
-// Kernel k (1..4 stage, 5 increment) of class c for state parity `par` on `st`.
+// Kernel k (1..4 stage, 5 increment, 6 moment fold) of class c for state parity
+// `par` on `st`.
 cudaError_t launch_kernel(cosenu_batch_t b, int ci, int k, int par, cudaStream_t st) {
   const ClassPlan& c = b->classes[ci];
   if (k == 5) {
     const ApplySeg* segs = reinterpret_cast<const ApplySeg*>(b->tables + c.seg_off);
     const int64_t* cf = reinterpret_cast<const int64_t*>(b->tables + c.chunk_off);
     const int64_t blocks = std::min<int64_t>(c.nchunks, (int64_t)b->nsm * 8);
-    apply_increment_batch_kernel<<<(int)blocks, 256, 0, st>>>(segs, cf, c.nseg, c.nchunks);
+    apply_increment_batch_kernel<<<(int)blocks, kApplyThreads, 0, st>>>(segs, cf, c.nseg,
+                                                                        c.nchunks);
+    return cudaGetLastError();
+  }
+  if (k == 6) {
+    const ApplySeg* segs = reinterpret_cast<const ApplySeg*>(b->tables + c.seg_off);
+    const int64_t* ff = reinterpret_cast<const int64_t*>(b->tables + c.fold_off);
+    const int64_t blocks = std::min<int64_t>(c.nfold, (int64_t)b->nsm * 8);
+    fold_moments_batch_kernel<<<(int)blocks, 256, 0, st>>>(segs, ff, c.nseg, c.nfold);
     return cudaGetLastError();
   }
   const StageCfg& cf = c.cfg[k];
@@ -335,10 +343,10 @@ cudaError_t launch_kernel(cosenu_batch_t b, int ci, int k, int par, cudaStream_t
 
 // One class's RK4 step on `st`; kernels bracketed by events when timing.
 cudaError_t enqueue_chain(cosenu_batch_t b, int ci, int par, cudaStream_t st, bool timed) {
-  const int nk = b->classes[ci].key.precision == COSENU_MIXED ? 5 : 4;
+  const int nk = b->classes[ci].key.precision == COSENU_MIXED ? 6 : 4;
   for (int k = 1; k <= nk; ++k) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (timed) {
+    if (timed && k <= 5) {  // the moment fold is not timed
       cudaError_t e = take_event(b, &e0);
       if (e == cudaSuccess) e = take_event(b, &e1);
       if (e == cudaSuccess) e = cudaEventRecord(e0, st);
@@ -347,7 +355,7 @@ cudaError_t enqueue_chain(cosenu_batch_t b, int ci, int par, cudaStream_t st, bo
     cudaError_t e = launch_kernel(b, ci, k, par, st);
     if (e != cudaSuccess) return e;
     if (!b->capturing) count_launches(1);
-    if (timed) {
+    if (timed && k <= 5) {
       e = cudaEventRecord(e1, st);
       if (e != cudaSuccess) return e;
       b->timed.push_back({ci, k, e0, e1});
@@ -403,7 +411,7 @@ int build_graph(cosenu_batch_t b) {
 // Launches one graph replay stands for (captured launches are counted per replay).
 int graph_launches(const cosenu_batch_t b) {
   int n = 0;
-  for (const ClassPlan& c : b->classes) n += c.key.precision == COSENU_MIXED ? 5 : 4;
+  for (const ClassPlan& c : b->classes) n += c.key.precision == COSENU_MIXED ? 6 : 4;
   return n * kGraphSteps;
 }
 

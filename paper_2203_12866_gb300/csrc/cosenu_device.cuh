@@ -55,7 +55,6 @@ struct StageArgs {
   const void* d1;         // FP64 stage 4: delta_1 (center rows only)
   const void* d2;         // FP64 stage 4: delta_2 (center rows only)
   double* my;             // mixed: running FP64 moments of y, [nz][8] (6 used)
-  float* mdel;            // mixed: float moments of delta_1, delta_2, [2][nz][8] (6 used)
   const double* vtab;     // beam velocities v_j [nv], then quadrature weights w_j [nv]
   uint32_t* err;          // device error flags
 };

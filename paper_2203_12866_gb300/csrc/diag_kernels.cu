@@ -82,67 +82,140 @@ __device__ __forceinline__ bool apply4(double2* __restrict__ y, float4* __restri
   return is_finite_bits(a.x) && is_finite_bits(a.y) && is_finite_bits(b.x) && is_finite_bits(b.y);
 }
 
-// Mixed path, end of an RK4 step: y <- y + increment in double and the float
-// copy y32 <- round(y), in place, element by element.  d1..d4 are the float
-// stage increments; n = 8 nz nv (a multiple of 4).
-__global__ void __launch_bounds__(256) apply_increment_kernel(
-    double* __restrict__ y, float* __restrict__ y32, const float* __restrict__ d1,
-    const float* __restrict__ d2, const float* __restrict__ d3, const float* __restrict__ d4,
-    int64_t n, uint32_t* err) {
+// Mixed path, end of an RK4 step, one chunk of plane-rows: y <- y + dy in
+// double and the float copy y32 <- round(y), in place, and the weighted v-sums
+// of dy of every plane-row of the chunk (pmom), from which the running FP64
+// v-moments of y advance (fold_moments_kernel).  dy is the float increment
+// formed per element; its v-sums are taken in a fixed order (each float4
+// group's four products, then the row's groups by lane and a butterfly), so
+// they depend only on the data and nv, not on the chunk or launch.
+__device__ __forceinline__ void apply_chunk(const ApplySeg& sg, int64_t ch, float2* sm) {
+  const int L = sg.nv >> 2;  // float4 groups per plane-row
+  const int64_t nprow = 8 * sg.nz;
+  const int64_t pr0 = ch * sg.rows_per_chunk;
+  const int nrow = (int)min((int64_t)sg.rows_per_chunk, nprow - pr0);
+  const int ng = nrow * L;
+  const int64_t g0 = pr0 * L;
+  const int tid = threadIdx.x;
   bool bad = false;
-  const int64_t n4 = n >> 2;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  // two float4 groups per thread and iteration: more loads in flight
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += 2 * stride) {
-    const int64_t i2 = i + stride;
-    const bool two = i2 < n4;
-    const float4 a1 = reinterpret_cast<const float4*>(d1)[i];
-    const float4 a2 = reinterpret_cast<const float4*>(d2)[i];
-    const float4 a3 = reinterpret_cast<const float4*>(d3)[i];
-    const float4 a4 = reinterpret_cast<const float4*>(d4)[i];
-    float4 b1 = a1, b2 = a2, b3 = a3, b4 = a4;
-    if (two) {
-      b1 = reinterpret_cast<const float4*>(d1)[i2];
-      b2 = reinterpret_cast<const float4*>(d2)[i2];
-      b3 = reinterpret_cast<const float4*>(d3)[i2];
-      b4 = reinterpret_cast<const float4*>(d4)[i2];
-    }
-    bad |= !apply4(reinterpret_cast<double2*>(y) + 2 * i, reinterpret_cast<float4*>(y32) + i,
-                   rk4_increment(a1, a2, a3, a4));
-    if (two)
-      bad |= !apply4(reinterpret_cast<double2*>(y) + 2 * i2, reinterpret_cast<float4*>(y32) + i2,
-                     rk4_increment(b1, b2, b3, b4));
+  // two groups per thread in flight
+  for (int g = tid; g < ng; g += 2 * kApplyThreads) {
+    const int gb = g + kApplyThreads;
+    const bool two = gb < ng;
+    const int64_t ia = g0 + g, ib = g0 + (two ? gb : g);
+    const float4 a1 = reinterpret_cast<const float4*>(sg.d[0])[ia];
+    const float4 a2 = reinterpret_cast<const float4*>(sg.d[1])[ia];
+    const float4 a3 = reinterpret_cast<const float4*>(sg.d[2])[ia];
+    const float4 a4 = reinterpret_cast<const float4*>(sg.d[3])[ia];
+    const float4 b1 = reinterpret_cast<const float4*>(sg.d[0])[ib];
+    const float4 b2 = reinterpret_cast<const float4*>(sg.d[1])[ib];
+    const float4 b3 = reinterpret_cast<const float4*>(sg.d[2])[ib];
+    const float4 b4 = reinterpret_cast<const float4*>(sg.d[3])[ib];
+    auto one = [&](int gg, int64_t i, float4 inc) {
+      bad |= !apply4(reinterpret_cast<double2*>(sg.y) + 2 * i, reinterpret_cast<float4*>(sg.y32) + i,
+                     inc);
+      const int r = gg / L;
+      const int v0 = (gg - r * L) * 4;
+      const float4 w = *reinterpret_cast<const float4*>(sg.wtab + v0);
+      const float4 wv = *reinterpret_cast<const float4*>(sg.wtab + sg.nv + v0);
+      sm[gg] = make_float2(((w.x * inc.x + w.y * inc.y) + w.z * inc.z) + w.w * inc.w,
+                           ((wv.x * inc.x + wv.y * inc.y) + wv.z * inc.z) + wv.w * inc.w);
+    };
+    one(g, ia, rk4_increment(a1, a2, a3, a4));
+    if (two) one(gb, ib, rk4_increment(b1, b2, b3, b4));
   }
-  if (__ballot_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, kErrNonFinite);
+  if (__ballot_sync(0xffffffffu, bad) && (tid & 31) == 0) atomicOr(sg.err, kErrNonFinite);
+  __syncthreads();
+  // Row sums: T adjacent lanes per plane-row (T a power of two, fixed by the
+  // chunk shape rows_per_chunk x L), each summing every T-th group of the row in
+  // ascending order, then a butterfly over the T lanes.
+  int T = kApplyThreads / sg.rows_per_chunk;
+  T = T >= 32 ? 32 : T >= 16 ? 16 : T >= 8 ? 8 : T >= 4 ? 4 : T >= 2 ? 2 : 1;
+  const int sub = tid & (T - 1);
+  for (int base = 0; base < sg.rows_per_chunk; base += kApplyThreads / T) {  // uniform trip count
+    const int r = base + tid / T;
+    float s0 = 0.0f, s1 = 0.0f;
+    if (r < nrow) {
+      for (int l = sub; l < L; l += T) {
+        const float2 t = sm[r * L + l];
+        s0 += t.x;
+        s1 += t.y;
+      }
+    }
+    for (int o = T >> 1; o > 0; o >>= 1) {
+      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    }
+    if (sub == 0 && r < nrow) sg.pmom[pr0 + r] = make_float2(s0, s1);
+  }
+  __syncthreads();  // sm is reused by the next chunk
 }
 
-// The same update for several states: segment k is cut into chunks of
-// kApplyChunk4 float4 groups, chunks chunk_first[k] .. chunk_first[k + 1] - 1
-// of the launch; blocks walk the chunks.  Non-finite results are reported in
-// the segment's own error word.
-__global__ void __launch_bounds__(256) apply_increment_batch_kernel(
+__global__ void __launch_bounds__(kApplyThreads) apply_increment_kernel(ApplySeg sg) {
+  __shared__ float2 sm[kApplyGroups];
+  for (int64_t ch = blockIdx.x; ch < sg.nchunks; ch += gridDim.x) apply_chunk(sg, ch, sm);
+}
+
+// The same for several states: chunks chunk_first[k] .. chunk_first[k + 1] - 1
+// of the launch belong to segment k; blocks walk the chunks.  Non-finite
+// results are reported in the segment's own error word.
+__global__ void __launch_bounds__(kApplyThreads) apply_increment_batch_kernel(
     const ApplySeg* __restrict__ segs, const int64_t* __restrict__ chunk_first, int nseg,
     int64_t nchunks) {
+  __shared__ float2 sm[kApplyGroups];
   for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     int lo = 0, hi = nseg - 1;  // last segment whose first chunk is <= ch
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
       if (chunk_first[mid] <= ch) lo = mid; else hi = mid - 1;
     }
-    const ApplySeg sg = segs[lo];
-    const int64_t i0 = (ch - chunk_first[lo]) * kApplyChunk4;
-    const int64_t i1 = min(sg.n4, i0 + kApplyChunk4);
-    bool bad = false;
-    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
-      const float4 inc = rk4_increment(reinterpret_cast<const float4*>(sg.d[0])[i],
-                                       reinterpret_cast<const float4*>(sg.d[1])[i],
-                                       reinterpret_cast<const float4*>(sg.d[2])[i],
-                                       reinterpret_cast<const float4*>(sg.d[3])[i]);
-      bad |= !apply4(reinterpret_cast<double2*>(sg.y) + 2 * i,
-                     reinterpret_cast<float4*>(sg.y32) + i, inc);
+    apply_chunk(segs[lo], ch - chunk_first[lo], sm);
+  }
+}
+
+// my[z][k] += the z row's v-moments of the step's increment, from the eight
+// plane-row sums of (species, component): D3 = (ee - xx) - (ee - xx)bar,
+// Dr = Re - Re bar, Di = Im + Im bar (S - Sbar^*, Eq. (ham)), n = 0, 1; in double.
+__device__ __forceinline__ void fold_row(double* __restrict__ my, const float2* __restrict__ pmom,
+                                         int64_t nz, int64_t z) {
+  double p0[8], p1[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const float2 t = pmom[k * nz + z];
+    p0[k] = f2d_int(t.x);
+    p1[k] = f2d_int(t.y);
+  }
+  double* m = my + z * 8;
+  m[0] += (p0[0] - p0[1]) - (p0[4] - p0[5]);
+  m[1] += (p1[0] - p1[1]) - (p1[4] - p1[5]);
+  m[2] += p0[2] - p0[6];
+  m[3] += p1[2] - p1[6];
+  m[4] += p0[3] + p0[7];
+  m[5] += p1[3] + p1[7];
+}
+
+__global__ void fold_moments_kernel(double* __restrict__ my, const float2* __restrict__ pmom,
+                                    int64_t nz) {
+  for (int64_t z = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; z < nz;
+       z += (int64_t)gridDim.x * blockDim.x)
+    fold_row(my, pmom, nz, z);
+}
+
+// The same for several states: blocks block_first[k] .. block_first[k + 1] - 1
+// of the launch fold kFoldRows rows each of segment k.
+__global__ void fold_moments_batch_kernel(const ApplySeg* __restrict__ segs,
+                                          const int64_t* __restrict__ block_first, int nseg,
+                                          int64_t nblocks) {
+  for (int64_t b = blockIdx.x; b < nblocks; b += gridDim.x) {
+    int lo = 0, hi = nseg - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (block_first[mid] <= b) lo = mid; else hi = mid - 1;
     }
-    if (__ballot_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0)
-      atomicOr(sg.err, kErrNonFinite);
+    const ApplySeg& sg = segs[lo];
+    const int64_t z0 = (b - block_first[lo]) * kFoldRows;
+    const int64_t z1 = min(sg.nz, z0 + kFoldRows);
+    for (int64_t z = z0 + threadIdx.x; z < z1; z += blockDim.x) fold_row(sg.my, sg.pmom, sg.nz, z);
   }
 }
 

@@ -10,28 +10,44 @@ namespace cosenu {
 
 constexpr int kDiagBlock = 256;
 constexpr int kDiagMaxBlocks = 1024;
-constexpr int64_t kApplyChunk4 = 1024;  // float4 groups per chunk of the batched increment
+constexpr int kApplyGroups = 1024;  // float4 groups per chunk of the increment kernels
+constexpr int kApplyThreads = 256;
+constexpr int kFoldRows = 1024;     // z rows per block of the batched moment fold
 
-// One state of the batched increment kernel: n4 = 2 nz nv float4 groups.
+// One mixed-precision state for the increment kernels.  The flat arrays are
+// [species][component][z][v]; a plane-row is one (species, component, z) run of
+// nv values, and a chunk is rows_per_chunk whole plane-rows (nv / 4 float4
+// groups each, at most kApplyGroups in all).
 struct ApplySeg {
   double* y;
   float* y32;
-  const float* d[4];  // the four stage increments
-  int64_t n4;
+  const float* d[4];    // the four stage increments
+  float2* pmom;         // [8 nz] per plane-row: sum_j w_j dy_j, sum_j w_j v_j dy_j
+  const float* wtab;    // [2][nv]: w_j, w_j v_j of the quadrature (float)
+  double* my;           // [nz][8] running FP64 v-moments of y
+  int64_t nz;
+  int32_t nv;
+  int32_t rows_per_chunk;
+  int64_t nchunks;      // ceil(8 nz / rows_per_chunk)
   uint32_t* err;
 };
+
+// Plane-rows per chunk of a grid with nv beams.
+inline int apply_rows_per_chunk(int nv) { return kApplyGroups / (nv / 4); }
 
 __global__ void ymoments_kernel(const double* __restrict__ y, int64_t nz, int nv,
                                 double* __restrict__ out, int stride, int vgrid);
 __global__ void y32_from_y_kernel(const double* __restrict__ y, float* __restrict__ y32,
                                   int64_t n);
-__global__ void apply_increment_kernel(double* __restrict__ y, float* __restrict__ y32,
-                                       const float* __restrict__ d1, const float* __restrict__ d2,
-                                       const float* __restrict__ d3, const float* __restrict__ d4,
-                                       int64_t n, uint32_t* err);
+__global__ void apply_increment_kernel(ApplySeg sg);
 __global__ void apply_increment_batch_kernel(const ApplySeg* __restrict__ segs,
                                              const int64_t* __restrict__ chunk_first, int nseg,
                                              int64_t nchunks);
+__global__ void fold_moments_kernel(double* __restrict__ my, const float2* __restrict__ pmom,
+                                    int64_t nz);
+__global__ void fold_moments_batch_kernel(const ApplySeg* __restrict__ segs,
+                                          const int64_t* __restrict__ block_first, int nseg,
+                                          int64_t nblocks);
 __global__ void collective_fill_kernel(double* __restrict__ y, int64_t nz, int nv,
                                        const double* __restrict__ g,
                                        const double* __restrict__ ph);

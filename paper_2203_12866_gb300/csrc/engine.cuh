@@ -22,7 +22,7 @@ struct StageCfg {
 
 // Byte offsets of a handle's buffers inside its workspace.
 struct Layout {
-  size_t y0, y1, y32a, y32b, d1, d2, d3, d4, my, mdel, zavg, vtab, partial, result, err, total;
+  size_t y0, y1, y32a, y32b, d1, d2, d3, d4, my, pmom, wtab, zavg, vtab, partial, result, err, total;
 };
 
 // One admissible ring shape of a stage kernel: R rows per slot, D slots.
@@ -52,7 +52,8 @@ struct cosenu_s {
   int ycur = 0;
   void* d[4] = {nullptr, nullptr, nullptr, nullptr};  // delta_1..3 (mixed: and delta_4)
   double* my = nullptr;
-  float* mdel = nullptr;   // mixed: float moments of delta_1, delta_2 per row
+  float2* pmom = nullptr;  // mixed: weighted v-sums of the step's increment per plane-row
+  float* wtab = nullptr;   // mixed: quadrature weights w_j and w_j v_j in float, [2][nv]
   double* vtab = nullptr;  // beam velocities [nv] and quadrature weights [nv]
   uint32_t* err = nullptr;
   cosenu::StageCfg cfg[5];
@@ -103,6 +104,10 @@ void destroy_member(cosenu_t h);
 // Arguments of stage `stage` of a handle whose current state buffer is `ycur`
 // (launch-shape fields from h->cfg).
 StageArgs stage_args(const cosenu_s* h, int stage, int ycur);
+
+// The handle's state and buffers as one segment of the increment kernels (mixed).
+struct ApplySeg;
+ApplySeg apply_seg(const cosenu_s* h);
 
 // Wait for the batch's stream; (*flags)[i] = error bits of member i (then
 // cleared on the device).

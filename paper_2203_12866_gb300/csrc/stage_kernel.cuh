@@ -9,7 +9,7 @@
 // In the mixed path stage 4 writes delta_4 = dt k_4 like the other stages, and
 // a separate streaming kernel, apply_increment_kernel, forms
 //   dy = (delta_1 + 2 delta_2 + delta_3) / 3 + delta_4 / 6
-// in float and performs y <- y + dy in double.
+// in float, performs y <- y + dy in double and sums the v-moments of dy.
 //
 // Work decomposition.  A CTA owns a contiguous range of z rows and all 2 nv
 // (species, v) columns, and marches along z with three warp roles:
@@ -32,7 +32,7 @@
 //  - FP64 path: D_n of u_s in double.
 //  - mixed path: D_n(u_s) = D_n(y) + D_n(delta_{s-1}).  D_n(y) is a per-z double
 //    running sum (set from y once, then advanced by D_n of each step's float
-//    increment in stage 4); D_n(delta) is summed in float.
+//    increment dy, which the increment kernels sum); D_n(delta) is summed in float.
 #pragma once
 
 #include <type_traits>
@@ -160,20 +160,18 @@ __host__ __device__ inline SlotLayout slot_layout(int nv, int stage, int R) {
 }
 
 // Shared memory besides the ring.  Acc is the type of the moment partials.
-//   mbarriers: full[kMaxRing] empty[kMaxRing] part[kMomSlots] mom[kMomSlots] dy[kMomSlots]
-//   flags (abort), partials [kMomSlots][NW consumer warps][8] Acc, delta_4 moment
-//   partials (mixed only, same shape), finished moments [kMomSlots][8] Acc, running moments of
-//   y (mixed) [kMomSlots][8] double.
+//   mbarriers: full[kMaxRing] empty[kMaxRing] part[kMomSlots] mom[kMomSlots]
+//   flags (abort), partials [kMomSlots][NW consumer warps][8] Acc, finished
+//   moments [kMomSlots][8] Acc, running moments of y (mixed) [kMomSlots][8] double.
 template <int PREC, int NW>
 struct SmemHeader {
   using Acc = typename Prec<PREC>::Real;
   static constexpr int kBars = 0;
-  static constexpr int kNumBars = 2 * kMaxRing + 3 * kMomSlots;
+  static constexpr int kNumBars = 2 * kMaxRing + 2 * kMomSlots;
   static constexpr int kFlags = kBars + kNumBars * 8;
   static constexpr int kPart = ((kFlags + 64) + 127) & ~127;
   static constexpr int kPartBytes = kMomSlots * NW * 8 * (int)sizeof(Acc);
-  static constexpr int kPartDy = kPart + kPartBytes;
-  static constexpr int kMomf = kPartDy + (PREC == kMIXED ? kPartBytes : 0);
+  static constexpr int kMomf = kPart + kPartBytes;
   static constexpr int kMyRing = kMomf + kMomSlots * 8 * (int)sizeof(Acc);
   static constexpr int kBytes = ((kMyRing + kMomSlots * 8 * 8) + 127) & ~127;
 };
