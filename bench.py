@@ -287,6 +287,57 @@ def run_variant(b, scheme, prec, steps, warmup, device, stream, state_dev):
         b.cosenu_destroy(h)
 
 
+# The two smaller configurations of the method's workloads (nz, nv, L, steps per
+# timed run for mixed / FP64, legs).  The first is L2-resident and launch-bound:
+# its steps replay a CUDA graph, reported as microseconds per step.
+SMALL_CONFIGS = (
+    ("nz=512, nv=32, z in [-50, 50), mu=1", 512, 32, 100.0, (400, 400),
+     (("fdko", "fp64"), ("fdko", "mixed"), ("weno7", "fp64"), ("weno7", "mixed"))),
+    ("nz=65536, nv=128, z in [-1600, 1600), mu=1", 65536, 128, 3200.0, (20, 4),
+     (("fdko", "mixed"), ("weno7", "mixed"), ("fdko", "fp64"), ("weno7", "fp64"))),
+)
+
+
+def run_small_configs(b, device, stream):
+    """Per-step time of the smaller configurations (alpha=0.9, sigma=(0.6, 0.5),
+    random-phase seed 1e-6, dt = 0.4 dz), steps replayed from the handle's graph."""
+    import torch
+
+    from paper_2203_12866_gb300 import inputs
+    out = {}
+    for label, nz, nv, lz, (k_mixed, k_fp64), legs in SMALL_CONFIGS:
+        with torch.cuda.stream(stream):
+            st = inputs.collective_state_device(nz, nv, device, alpha=ALPHA, sigma_nu=SIG_NU,
+                                                sigma_nubar=SIG_NUBAR, eps0=EPS0, seed=SEED)
+        stream.synchronize()
+        for sc, pr in legs:
+            k = k_mixed if pr == "mixed" else k_fp64
+            h = b.cosenu_create(nz, nv, lz, SCHEMES[sc], PRECS[pr])
+            try:
+                b.cosenu_set_stream(h, stream.cuda_stream)
+                b.cosenu_set_params(h, mu=1.0)
+                b.cosenu_set_state_device(h, st.data_ptr(), st.numel())
+                b.cosenu_step(h, 4)
+                b.cosenu_sync(h)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                b.cosenu_step(h, k)
+                e1.record(stream)
+                e1.synchronize()
+                if b.cosenu_sync(h) != 0:
+                    raise RuntimeError(f"{label} {sc} {pr}: solver error")
+                ms = e0.elapsed_time(e1) / k
+            finally:
+                b.cosenu_destroy(h)
+            out[f"{sc}_{pr}_{nz}x{nv}"] = {"workload": label, "scheme": sc, "precision": pr,
+                                           "steps": k, "us_per_step": ms * 1e3,
+                                           "cell_updates_per_s": 2 * nz * nv / (ms * 1e-3)}
+        del st
+    torch.cuda.empty_cache()
+    return out
+
+
 BATCH_WORKLOAD = ("batched run: 256 independent grids, nz log-uniform [1024, 32768], "
                   "nv in {32, 64, 128}, mu log-uniform [0.1, 10], alpha U[0.7, 1.2], "
                   "sigma_nu, sigma_nubar U[0.3, 0.8], scheme FD+KO or WENO7 at random, "
@@ -532,6 +583,7 @@ def run_ours(args, world, rank, local):
     del state
     torch.cuda.empty_cache()
 
+    small = run_small_configs(b, device, stream) if args.variants else None
     batched = run_batched(args, device, hbm_peak) if args.batched else None
     serving = run_serving(args) if args.serving and rank == 0 else None
 
@@ -556,7 +608,8 @@ def run_ours(args, world, rank, local):
                        "l2": "inputs larger than L2 (state 17.2 GB >> 129 MB)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clk, "variants": variants, "batched": batched, "serving": serving,
+            "clocks": clk, "variants": variants, "small_configs": small, "batched": batched,
+            "serving": serving,
             "conserved_after": {"tr_nu": cons["tr_nu"], "M": list(cons["M"]),
                                 "dP_max": cons["dP_max"]},
         }

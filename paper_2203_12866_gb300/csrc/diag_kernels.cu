@@ -151,7 +151,7 @@ __device__ __forceinline__ void apply_chunk(const ApplySeg& sg, int64_t ch, floa
   __syncthreads();  // sm is reused by the next chunk
 }
 
-__global__ void __launch_bounds__(kApplyThreads) apply_increment_kernel(ApplySeg sg) {
+__global__ void __launch_bounds__(kApplyThreads, 4) apply_increment_kernel(ApplySeg sg) {
   __shared__ float2 sm[kApplyGroups];
   for (int64_t ch = blockIdx.x; ch < sg.nchunks; ch += gridDim.x) apply_chunk(sg, ch, sm);
 }
@@ -159,7 +159,7 @@ __global__ void __launch_bounds__(kApplyThreads) apply_increment_kernel(ApplySeg
 // The same for several states: chunks chunk_first[k] .. chunk_first[k + 1] - 1
 // of the launch belong to segment k; blocks walk the chunks.  Non-finite
 // results are reported in the segment's own error word.
-__global__ void __launch_bounds__(kApplyThreads) apply_increment_batch_kernel(
+__global__ void __launch_bounds__(kApplyThreads, 4) apply_increment_batch_kernel(
     const ApplySeg* __restrict__ segs, const int64_t* __restrict__ chunk_first, int nseg,
     int64_t nchunks) {
   __shared__ float2 sm[kApplyGroups];

@@ -218,7 +218,19 @@ __device__ __forceinline__ int64_t wrap_row(int64_t r, int64_t nz) {
 // The square roots of 20/3 and 260 are folded into the coefficients of a and b,
 // the linear weights into those of delta_r.
 
-// double: one division per face.  With q_r = (SI_r + eps)^2 the normalised
+// Reciprocal of a positive normal double: the special-function unit's
+// approximation refined by two Newton-Raphson steps r <- r (2 - d r) (each
+// squares the relative error), a few ulp from the correctly rounded 1 / d.
+__device__ __forceinline__ double rcp_newton(double d) {
+  double r;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(d));
+  double e = fma(-d, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-d, r, 1.0);
+  return fma(r, e, r);
+}
+
+// double: one reciprocal per face.  With q_r = (SI_r + eps)^2 the normalised
 // weights d_r / q_r / sum_k (d_k / q_k) equal d_r prod_{k!=r} q_k /
 // sum_j d_j prod_{k!=j} q_k (q_r >= eps^2 keeps the products in range).
 __device__ __forceinline__ double weno7_face(double fm3, double fm2, double fm1, double f0,
@@ -250,7 +262,7 @@ __device__ __forceinline__ double weno7_face(double fm3, double fm2, double fm1,
   const double p0 = q1 * q23, p1 = q0 * q23, p2 = q01 * q3, p3 = q01 * q2;
   const double num = p0 * dd0 + p1 * dd1 + p2 * dd2 + p3 * dd3;
   const double den = (4.0 / 35.0) * p0 + (18.0 / 35.0) * p1 + (12.0 / 35.0) * p2 + (1.0 / 35.0) * p3;
-  return f0 + num / den;
+  return fma(num, rcp_newton(den), f0);
 }
 
 // Approximate reciprocal (the special-function unit's, relative error ~2^-23;
