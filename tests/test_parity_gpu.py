@@ -62,6 +62,19 @@ def test_fp64_ragged_tiles(scheme, nz, nv):
 
 
 @pytest.mark.parametrize("scheme", ["fdko", "weno7", "fdko3"])
+@pytest.mark.parametrize("nz,nv", [(37, 36), (53, 12), (200, 100), (61, 4)])
+def test_mixed_ragged_tiles(scheme, nz, nv):
+    """Mixed path on ragged shapes: odd row counts per CTA (the two-row march of
+    mixed WENO7 ends on a single row), and v-row lengths whose increment-kernel
+    chunks hold a non-power-of-two number of plane-rows (nv = 36: 113 rows of 9
+    groups; nv = 12: 341 of 3; nv = 100: 40 of 25; nv = 4: 1024 of 1)."""
+    u0 = inputs.random_state(nz, nv, seed=nz + nv, offdiag=0.05)
+    got = run_gpu(u0, 0.2 * nz, SCHEMES[scheme], PRECS["mixed"], 6, mu=0.7, omega=0.2, theta=0.3)
+    ref = run_oracle(u0, 0.2 * nz, SCHEMES[scheme], 6, mu=0.7, omega=0.2, theta=0.3)
+    assert max_abs(got, ref) <= 1e-5
+
+
+@pytest.mark.parametrize("scheme", ["fdko", "weno7", "fdko3"])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("nz", [1, 2, 3, 5, 9])
 def test_tiny_periodic_grids(scheme, prec, nz):
