@@ -66,6 +66,7 @@ KERNEL_NAMES = ("stage 1", "stage 2", "stage 3", "stage 4", "increment")
 FP64_FLOPS_PER_CELL = {"fdko": (87, 91, 91, 119), "weno7": (533, 537, 537, 565)}
 SCHEMES = {"fdko": 0, "weno7": 1}
 PRECS = {"fp64": 0, "mixed": 1}
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal (the measured copy bandwidth is the peak used)
 # 152 SMs x 2 FP64 FMA lanes per clock x 2 flops x 2.07 GHz (nominal 1.25 TFLOP/s)
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
@@ -532,7 +533,8 @@ def run_ours(args, world, rank, local):
                 "frac": dom["hbm_frac"], "traffic": traffic,
                 "kernel": (f"rk4_stage_kernel<{scheme},{prec},stage {dom['stage']}>"
                            if dom["stage"] <= 4 else "apply_increment_kernel"),
-                "peak_kind": f"{peak_kind} (copy)", "stages": stages,
+                "peak_kind": f"{peak_kind} (copy)", "frac_of_nominal": dom["GB/s"] / NOMINAL_HBM_GBS,
+                "stages": stages,
                 "step_frac": (sum(STAGE_BYTES[prec]) * 8 * NZ * NV / (ms_step * 1e-3) / 1e9)
                 / hbm_peak}
 
