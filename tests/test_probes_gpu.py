@@ -1,7 +1,8 @@
 """GPU probes of device helpers that the end-to-end parity tests only see
 indirectly: the integer double <-> float conversions of the mixed path are
-compared bit for bit with the hardware conversions, and the reciprocals of the
-WENO7 weights with correctly rounded division."""
+compared bit for bit with the hardware conversions, the reciprocals of the
+WENO7 weights with correctly rounded division, and the bounded device-side wait
+is made to run out (a barrier nothing completes) without faulting the GPU."""
 import os
 import subprocess
 
@@ -33,3 +34,22 @@ def test_weno_reciprocals_against_division(tmp_path):
     assert ulp_d <= 4, ulp_d
     # the SFU float reciprocal: within 2 ulp of 1/f
     assert ulp_f <= 2, ulp_f
+
+
+def test_bounded_wait_gives_up_and_raises_abort(tmp_path):
+    """Failure detection on the device without a fault: the stage kernels' bounded
+    mbarrier wait on a barrier that nothing completes returns false after the wait
+    limit (about 2 s of SM clocks) and sets the timeout bit that cosenu_sync reports
+    as COSENU_ETIMEOUT; a second warp waiting elsewhere leaves on the abort flag
+    before its own limit; the context stays usable."""
+    exe = str(tmp_path / "wait_check")
+    subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17",
+                    "-I", os.path.join(ROOT, "paper_2203_12866_gb300", "csrc"),
+                    os.path.join(HERE, "gpu_probes", "wait_check.cu"), "-o", exe], check=True)
+    out = subprocess.run([exe], check=True, capture_output=True, text=True,
+                         timeout=120).stdout.split()
+    ok0, ok1, err, waited1, limit = (int(x) for x in out[:5])
+    assert ok0 == 0 and ok1 == 0
+    assert err == 2  # the timeout bit (kErrTimeout), nothing else
+    assert 0 < waited1 < limit  # warp 1 left on the abort flag, before its own limit
+    assert out[5] == "usable"
