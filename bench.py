@@ -46,24 +46,24 @@ WORKLOAD = ("roofline run: nz=2^20, nv=256, z in [-25600,25600), dt=0.4 dz, mu=1
             "alpha=0.9, sigma=(0.6,0.5), random-phase seed 1e-6")
 
 # Algorithmic HBM bytes per real component per launch of each kernel of an RK4
-# step (k = 1..4 the fused stage kernels, k = 5 the mixed path's increment kernel).
-# fp64 (all arrays double): stage 1 reads y, writes d1; stage 2 reads y, d1,
-#   writes d2; stage 3 reads y, d2, writes d3; stage 4 reads y, d3, d1, d2 and
-#   writes the new y.
-# mixed (state y double plus its float copy y32; increments float): stages 1-3
-#   read y32 instead of y; stage 4 reads y32, d3 and writes d4; the increment
-#   kernel reads y, d1, d2, d3, d4 and writes y, y32.
-STAGE_BYTES = {"fp64": (16, 24, 24, 40, 0), "mixed": (8, 12, 12, 12, 36)}
+# step (k = 1..4 the fused stage kernels, k = 5 the increment kernel).
+# fp64 (all arrays double): stage 1 reads y, writes d1; stage s = 2..4 reads y,
+#   d_{s-1}, writes d_s; the increment kernel reads y, d1..d4 and writes the new
+#   y into the other state buffer.
+# mixed (state y double plus its float copy y32; increments float): stages 1-4
+#   read y32 instead of y; the increment kernel reads y, d1..d4 and writes y,
+#   y32 in place.
+STAGE_BYTES = {"fp64": (16, 24, 24, 24, 48), "mixed": (8, 12, 12, 12, 36)}
 KERNEL_NAMES = ("stage 1", "stage 2", "stage 3", "stage 4", "increment")
-# FP64 flops per cell (4 reals) per launch of the fp64 stages, counted from the
-# kernels' arithmetic (FMA = 2 flops, a division = 1): stage input y + delta 4
+# FP64 flops per cell (4 reals) per launch of the fp64 kernels, counted from the
+# kernels' arithmetic (FMA = 2 flops, a reciprocal = 1): stage input y + delta 4
 # (stages 2-4), v-moment partials with the warp reduction 20 (FD4+KO, two
-# columns per thread) or 26 (WENO7, one), Hamiltonian 12, commutator 11,
-# advection 40 (FD4+KO: one FMA per window row, the two stencils combined) or
-# 480 (WENO7: 116 per face for the reconstruction in differences, 4 for the
-# flux difference), output 4 (delta_s) or 32 (stage 4: the RK4 combination and
-# y update).
-FP64_FLOPS_PER_CELL = {"fdko": (87, 91, 91, 119), "weno7": (533, 537, 537, 565)}
+# columns per thread) or 26 (WENO7, one), Hamiltonian 6 (one FMA per component
+# from the reducer's coefficients), commutator 11, advection 40 (FD4+KO: one
+# FMA per window row, the two stencils combined) or 484 (WENO7: 117 per face
+# for the reconstruction in differences, 4 for the flux difference), output 4
+# (delta_s); the increment kernel 32 (four FMA per real).
+FP64_FLOPS_PER_CELL = {"fdko": (81, 85, 85, 85, 32), "weno7": (531, 535, 535, 535, 32)}
 SCHEMES = {"fdko": 0, "weno7": 1}
 PRECS = {"fp64": 0, "mixed": 1}
 NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal (the measured copy bandwidth is the peak used)
@@ -254,7 +254,7 @@ def stage_roofline(stage_ms, stage_n, prec, scheme, hbm_peak):
         gbs = byts / (avg_ms * 1e-3) / 1e9
         rec = {"kernel": KERNEL_NAMES[s], "stage": s + 1, "avg_ms": avg_ms, "alg_bytes": byts,
                "GB/s": gbs, "hbm_frac": gbs / hbm_peak, "total_ms": stage_ms[s]}
-        if prec == "fp64" and s < 4:
+        if prec == "fp64":
             fl = FP64_FLOPS_PER_CELL[scheme][s] * 2 * NZ * NV
             rec["fp64_tflops"] = fl / (avg_ms * 1e-3) / 1e12
             rec["fp64_alu_frac"] = rec["fp64_tflops"] / FP64_PEAK_TFLOPS

@@ -219,10 +219,10 @@ int cosenu_spectrum(cosenu_t h, int32_t species, int32_t v_index, int64_t m0, in
  * is bracketed by CUDA events on the handle's stream (and steps are launched
  * directly rather than replayed from a graph).  cosenu_stage_times waits for
  * the stream and returns, per kernel k of an RK4 step (k = 1..4: the fused
- * stage kernels; k = 5: the mixed path's state-increment kernel, zero launches
- * in the FP64 path; the small kernel after it that folds the increment's
- * v-moments into the running moments of y is not timed), the summed device
- * time in milliseconds ms[k-1] and the
+ * stage kernels; k = 5: the state-increment kernel that ends the step; in the
+ * mixed path the small kernel after it that folds the increment's v-moments
+ * into the running moments of y is not timed), the summed device time in
+ * milliseconds ms[k-1] and the
  * number of timed launches n[k-1] since the last call (arrays of 5; either
  * pointer may be NULL), then clears the sums. */
 int cosenu_set_stage_timing(cosenu_t h, int on);
@@ -245,8 +245,8 @@ uint64_t cosenu_kernel_launches(void);
  * state after n batched steps is bit-identical to the same handle stepped n
  * times alone.  Members are grouped into classes of equal (scheme, precision,
  * nv); each class runs one fused kernel per RK4 stage over all of its members'
- * z rows (work items of whole or partial grids per CTA), plus, for the mixed
- * precision, one state-increment kernel per class.  Classes are independent
+ * z rows (work items of whole or partial grids per CTA), plus one
+ * state-increment kernel per class (and, mixed, one moment fold).  Classes are independent
  * chains of kernels, replayed from one CUDA graph as parallel branches.
  *
  * Member handles are created by the batch and share its stream.  Use the

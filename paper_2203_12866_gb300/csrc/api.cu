@@ -58,8 +58,7 @@ Layout make_layout(int64_t nz, int32_t nv, int precision) {
   L.d1 = off; off = align_up(off + n * dsz);
   L.d2 = off; off = align_up(off + n * dsz);
   L.d3 = off; off = align_up(off + n * dsz);
-  const size_t n4 = precision == COSENU_MIXED ? n : 0;  // delta_4 (mixed)
-  L.d4 = off; off = align_up(off + n4 * dsz);
+  L.d4 = off; off = align_up(off + n * dsz);
   L.my = off; off = align_up(off + (size_t)nz * 8 * sizeof(double));
   const size_t npm = precision == COSENU_MIXED ? (size_t)8 * nz : 0;
   L.pmom = off; off = align_up(off + npm * sizeof(float2));
@@ -205,8 +204,7 @@ bool stage_args_complete(int precision, int stage, const StageArgs& a) {
   const bool mixed = precision == COSENU_MIXED;
   if (!a.err || !a.vtab || (mixed ? !a.y32_in || !a.my : !a.y_in)) return false;
   if (stage > 1 && !a.d_in) return false;
-  if ((stage < 4 || mixed) && !a.d_out) return false;
-  if (stage == 4 && !mixed && (!a.d1 || !a.d2 || !a.y_out)) return false;
+  if (!a.d_out) return false;
   return true;
 }
 
@@ -295,7 +293,6 @@ StageArgs stage_args(const cosenu_s* h, int stage, int ycur) {
   a.ko_eps = h->p.ko_eps;
   a.weno_eps = h->p.weno_eps;
   a.y_in = h->y[ycur];
-  a.y_out = h->y[ycur ^ 1];
   a.y32_in = h->y32[0];
   a.my = h->my;
   a.err = h->err;
@@ -303,8 +300,8 @@ StageArgs stage_args(const cosenu_s* h, int stage, int ycur) {
     case 1: a.d_out = h->d[0]; break;
     case 2: a.d_in = h->d[0]; a.d_out = h->d[1]; break;
     case 3: a.d_in = h->d[1]; a.d_out = h->d[2]; break;
-    default:  // FP64: y from the center rows of delta_1, delta_2; mixed: delta_4
-      a.d_in = h->d[2]; a.d1 = h->d[0]; a.d2 = h->d[1]; a.d_out = h->d[3]; break;
+    default:
+      a.d_in = h->d[2]; a.d_out = h->d[3]; break;
   }
   return a;
 }
@@ -340,10 +337,18 @@ cudaError_t take_event(cosenu_t h, cudaEvent_t* out) {
 }
 
 
-// End of a mixed RK4 step: y <- y + dy with the plane-row v-sums of dy
+// End of an RK4 step.  FP64 (kernel 5): y[ycur ^ 1] = y[ycur] + the step's
+// increment.  Mixed: y <- y + dy in place with the plane-row v-sums of dy
 // (kernel 5), then the running FP64 moments of y advanced by them (kernel 6).
-cudaError_t launch_apply(cosenu_t h, int k) {
-  if (k == 5) {
+cudaError_t launch_apply(cosenu_t h, int k, int ycur) {
+  if (h->precision == COSENU_FP64) {
+    const int64_t n2 = 4 * h->nz * (int64_t)h->nv;  // double2 groups
+    const int64_t blocks = std::min<int64_t>((n2 + 255) / 256, (int64_t)h->nsm * 8);
+    apply_increment_fp64_kernel<<<(int)blocks, 256, 0, h->stream>>>(
+        h->y[ycur], h->y[ycur ^ 1], static_cast<const double*>(h->d[0]),
+        static_cast<const double*>(h->d[1]), static_cast<const double*>(h->d[2]),
+        static_cast<const double*>(h->d[3]), n2, h->err);
+  } else if (k == 5) {
     const ApplySeg sg = apply_seg(h);
     const int64_t blocks = std::min<int64_t>(sg.nchunks, (int64_t)h->nsm * 8);
     apply_increment_kernel<<<(int)blocks, kApplyThreads, 0, h->stream>>>(sg);
@@ -356,14 +361,14 @@ cudaError_t launch_apply(cosenu_t h, int k) {
   return e;
 }
 
-// One RK4 step: stages 1-4, then (mixed) the increment kernel and the moment
-// fold.  Kernels 1..5 of the step (stages, increment) are bracketed by events
-// when timing is on; the fold (a few hundredths of a millisecond) is not.
+// One RK4 step: stages 1-4, the increment kernel and (mixed) the moment fold.
+// Kernels 1..5 of the step (stages, increment) are bracketed by events when
+// timing is on; the fold (a few hundredths of a millisecond) is not.
 cudaError_t enqueue_step(cosenu_t h, int ycur) {
-  const int nk = h->precision == COSENU_MIXED ? 6 : 4;
+  const int nk = h->precision == COSENU_MIXED ? 6 : 5;
   for (int s = 1; s <= nk; ++s) {
     if (s == 6) {
-      cudaError_t e = launch_apply(h, 6);
+      cudaError_t e = launch_apply(h, 6, ycur);
       if (e != cudaSuccess) return e;
       continue;
     }
@@ -374,7 +379,7 @@ cudaError_t enqueue_step(cosenu_t h, int ycur) {
       if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
       if (e != cudaSuccess) return e;
     }
-    cudaError_t e = s <= 4 ? launch_stage(h, s, stage_args(h, s, ycur)) : launch_apply(h, 5);
+    cudaError_t e = s <= 4 ? launch_stage(h, s, stage_args(h, s, ycur)) : launch_apply(h, 5, ycur);
     if (e != cudaSuccess) return e;
     if (h->timing) {
       e = cudaEventRecord(e1, h->stream);
@@ -501,8 +506,8 @@ cosenu_t create_common(int64_t nz, int32_t nv, double L, int scheme, int precisi
   h->d[0] = h->ws + h->lay.d1;
   h->d[1] = h->ws + h->lay.d2;
   h->d[2] = h->ws + h->lay.d3;
+  h->d[3] = h->ws + h->lay.d4;
   if (precision == COSENU_MIXED) {
-    h->d[3] = h->ws + h->lay.d4;
     h->pmom = reinterpret_cast<float2*>(h->ws + h->lay.pmom);
     h->wtab = reinterpret_cast<float*>(h->ws + h->lay.wtab);
   }

@@ -61,6 +61,7 @@ struct ClassPlan {
   int occ[5] = {};
   size_t inst_off[5][2] = {}, item_off[5] = {};
   size_t seg_off = 0, chunk_off = 0, fold_off = 0;
+  size_t seg64_off[2] = {};  // FP64: increment segments per state parity
   int nseg = 0;
   int64_t nchunks = 0, nfold = 0;  // increment chunks, fold blocks
   double kernel_ms[6] = {};  // mean device time per launch at the last cosenu_batch_stage_times
@@ -223,6 +224,30 @@ int write_tables(cosenu_batch_t b) {
       c.seg_off = img.put(segs.data(), segs.size() * sizeof(ApplySeg));
       c.chunk_off = img.put(chunk_first.data(), chunk_first.size() * sizeof(int64_t));
       c.fold_off = img.put(fold_first.data(), fold_first.size() * sizeof(int64_t));
+    } else {
+      std::vector<int64_t> chunk_first;
+      for (int mi : c.members) {
+        const cosenu_t h = b->members[mi];
+        chunk_first.push_back(c.nchunks);
+        c.nchunks += (4 * h->nz * (int64_t)h->nv + kApplyGroups - 1) / kApplyGroups;
+      }
+      chunk_first.push_back(c.nchunks);
+      for (int par = 0; par < 2; ++par) {
+        std::vector<ApplySeg64> segs;
+        for (int mi : c.members) {
+          const cosenu_t h = b->members[mi];
+          ApplySeg64 sg;
+          sg.y_in = h->y[par];
+          sg.y_out = h->y[par ^ 1];
+          for (int k = 0; k < 4; ++k) sg.d[k] = static_cast<const double*>(h->d[k]);
+          sg.n2 = 4 * h->nz * (int64_t)h->nv;
+          sg.err = h->err;
+          segs.push_back(sg);
+        }
+        c.seg64_off[par] = img.put(segs.data(), segs.size() * sizeof(ApplySeg64));
+      }
+      c.nseg = (int)c.members.size();
+      c.chunk_off = img.put(chunk_first.data(), chunk_first.size() * sizeof(int64_t));
     }
   }
   // error flags: every member's word
@@ -316,6 +341,13 @@ cudaError_t take_event(cosenu_batch_t b, cudaEvent_t* out) {
 // `par` on `st`.
 cudaError_t launch_kernel(cosenu_batch_t b, int ci, int k, int par, cudaStream_t st) {
   const ClassPlan& c = b->classes[ci];
+  if (k == 5 && c.key.precision == COSENU_FP64) {
+    const ApplySeg64* segs = reinterpret_cast<const ApplySeg64*>(b->tables + c.seg64_off[par]);
+    const int64_t* cf = reinterpret_cast<const int64_t*>(b->tables + c.chunk_off);
+    const int64_t blocks = std::min<int64_t>(c.nchunks, (int64_t)b->nsm * 8);
+    apply_increment_fp64_batch_kernel<<<(int)blocks, 256, 0, st>>>(segs, cf, c.nseg, c.nchunks);
+    return cudaGetLastError();
+  }
   if (k == 5) {
     const ApplySeg* segs = reinterpret_cast<const ApplySeg*>(b->tables + c.seg_off);
     const int64_t* cf = reinterpret_cast<const int64_t*>(b->tables + c.chunk_off);
@@ -343,7 +375,7 @@ cudaError_t launch_kernel(cosenu_batch_t b, int ci, int k, int par, cudaStream_t
 
 // One class's RK4 step on `st`; kernels bracketed by events when timing.
 cudaError_t enqueue_chain(cosenu_batch_t b, int ci, int par, cudaStream_t st, bool timed) {
-  const int nk = b->classes[ci].key.precision == COSENU_MIXED ? 6 : 4;
+  const int nk = b->classes[ci].key.precision == COSENU_MIXED ? 6 : 5;
   for (int k = 1; k <= nk; ++k) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (timed && k <= 5) {  // the moment fold is not timed
@@ -411,7 +443,7 @@ int build_graph(cosenu_batch_t b) {
 // Launches one graph replay stands for (captured launches are counted per replay).
 int graph_launches(const cosenu_batch_t b) {
   int n = 0;
-  for (const ClassPlan& c : b->classes) n += c.key.precision == COSENU_MIXED ? 6 : 4;
+  for (const ClassPlan& c : b->classes) n += c.key.precision == COSENU_MIXED ? 6 : 5;
   return n * kGraphSteps;
 }
 

@@ -48,12 +48,9 @@ struct StageArgs {
   double ko_eps;
   double weno_eps;
   const double* y_in;     // fp64: state at the start of the step (read with halo)
-  double* y_out;          // fp64, stage 4: state at the end of the step
   const float* y32_in;    // mixed: float copy of the state (read with halo)
   const void* d_in;       // stage s > 1: delta_{s-1} (read with halo)
-  void* d_out;            // delta_s (stages 1-3; mixed stage 4: delta_4)
-  const void* d1;         // FP64 stage 4: delta_1 (center rows only)
-  const void* d2;         // FP64 stage 4: delta_2 (center rows only)
+  void* d_out;            // delta_s
   double* my;             // mixed: running FP64 moments of y, [nz][8] (6 used)
   const double* vtab;     // beam velocities v_j [nv], then quadrature weights w_j [nv]
   uint32_t* err;          // device error flags

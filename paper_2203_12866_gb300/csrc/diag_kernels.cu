@@ -173,6 +173,73 @@ __global__ void __launch_bounds__(kApplyThreads, 4) apply_increment_batch_kernel
   }
 }
 
+// FP64 end of an RK4 step, element by element into the other state buffer:
+//   y_out = y_in + (delta_1 + 2 delta_2 + delta_3) / 3 + delta_4 / 6
+//         = y_in + (2 delta_1 + 4 delta_2 + 2 delta_3 + delta_4) / 6.
+// Returns false if a result is not finite.
+__device__ __forceinline__ bool apply_fp64(const double2* __restrict__ y_in,
+                                           double2* __restrict__ y_out, double2 a, double2 b,
+                                           double2 c, double2 d, int64_t i) {
+  const double2 y = y_in[i];
+  double2 r;
+  r.x = fma(fma(2.0, c.x, fma(4.0, b.x, fma(2.0, a.x, d.x))), 1.0 / 6.0, y.x);
+  r.y = fma(fma(2.0, c.y, fma(4.0, b.y, fma(2.0, a.y, d.y))), 1.0 / 6.0, y.y);
+  y_out[i] = r;
+  return is_finite_bits(r.x) && is_finite_bits(r.y);
+}
+
+__global__ void __launch_bounds__(256) apply_increment_fp64_kernel(
+    const double* __restrict__ y_in, double* __restrict__ y_out, const double* __restrict__ d1,
+    const double* __restrict__ d2, const double* __restrict__ d3, const double* __restrict__ d4,
+    int64_t n2, uint32_t* err) {
+  const double2* a = reinterpret_cast<const double2*>(d1);
+  const double2* b = reinterpret_cast<const double2*>(d2);
+  const double2* c = reinterpret_cast<const double2*>(d3);
+  const double2* d = reinterpret_cast<const double2*>(d4);
+  const double2* yi = reinterpret_cast<const double2*>(y_in);
+  double2* yo = reinterpret_cast<double2*>(y_out);
+  bool bad = false;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  // two double2 groups per thread and iteration: more loads in flight
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += 2 * stride) {
+    const int64_t i2 = i + stride;
+    const bool two = i2 < n2;
+    const int64_t j = two ? i2 : i;
+    const double2 a1 = a[i], b1 = b[i], c1 = c[i], e1 = d[i];
+    const double2 a2 = a[j], b2 = b[j], c2 = c[j], e2 = d[j];
+    bad |= !apply_fp64(yi, yo, a1, b1, c1, e1, i);
+    if (two) bad |= !apply_fp64(yi, yo, a2, b2, c2, e2, i2);
+  }
+  if (__ballot_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, kErrNonFinite);
+}
+
+// The same for several states: chunks chunk_first[k] .. chunk_first[k + 1] - 1
+// (kApplyGroups double2 groups each) of the launch belong to segment k.
+__global__ void __launch_bounds__(256) apply_increment_fp64_batch_kernel(
+    const ApplySeg64* __restrict__ segs, const int64_t* __restrict__ chunk_first, int nseg,
+    int64_t nchunks) {
+  for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    int lo = 0, hi = nseg - 1;  // last segment whose first chunk is <= ch
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (chunk_first[mid] <= ch) lo = mid; else hi = mid - 1;
+    }
+    const ApplySeg64 sg = segs[lo];
+    const int64_t i0 = (ch - chunk_first[lo]) * kApplyGroups;
+    const int64_t i1 = min(sg.n2, i0 + kApplyGroups);
+    const double2* a = reinterpret_cast<const double2*>(sg.d[0]);
+    const double2* b = reinterpret_cast<const double2*>(sg.d[1]);
+    const double2* c = reinterpret_cast<const double2*>(sg.d[2]);
+    const double2* d = reinterpret_cast<const double2*>(sg.d[3]);
+    bool bad = false;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x)
+      bad |= !apply_fp64(reinterpret_cast<const double2*>(sg.y_in),
+                         reinterpret_cast<double2*>(sg.y_out), a[i], b[i], c[i], d[i], i);
+    if (__ballot_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0)
+      atomicOr(sg.err, kErrNonFinite);
+  }
+}
+
 // my[z][k] += the z row's v-moments of the step's increment, from the eight
 // plane-row sums of (species, component): D3 = (ee - xx) - (ee - xx)bar,
 // Dr = Re - Re bar, Di = Im + Im bar (S - Sbar^*, Eq. (ham)), n = 0, 1; in double.

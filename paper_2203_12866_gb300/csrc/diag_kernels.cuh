@@ -32,6 +32,15 @@ struct ApplySeg {
   uint32_t* err;
 };
 
+// One FP64 state for the FP64 increment kernel: n2 = 4 nz nv double2 groups.
+struct ApplySeg64 {
+  const double* y_in;
+  double* y_out;
+  const double* d[4];  // the four stage increments
+  int64_t n2;
+  uint32_t* err;
+};
+
 // Plane-rows per chunk of a grid with nv beams.
 inline int apply_rows_per_chunk(int nv) { return kApplyGroups / (nv / 4); }
 
@@ -43,6 +52,16 @@ __global__ void apply_increment_kernel(ApplySeg sg);
 __global__ void apply_increment_batch_kernel(const ApplySeg* __restrict__ segs,
                                              const int64_t* __restrict__ chunk_first, int nseg,
                                              int64_t nchunks);
+__global__ void apply_increment_fp64_kernel(const double* __restrict__ y_in,
+                                            double* __restrict__ y_out,
+                                            const double* __restrict__ d1,
+                                            const double* __restrict__ d2,
+                                            const double* __restrict__ d3,
+                                            const double* __restrict__ d4, int64_t n2,
+                                            uint32_t* err);
+__global__ void apply_increment_fp64_batch_kernel(const ApplySeg64* __restrict__ segs,
+                                                  const int64_t* __restrict__ chunk_first,
+                                                  int nseg, int64_t nchunks);
 __global__ void fold_moments_kernel(double* __restrict__ my, const float2* __restrict__ pmom,
                                     int64_t nz);
 __global__ void fold_moments_batch_kernel(const ApplySeg* __restrict__ segs,

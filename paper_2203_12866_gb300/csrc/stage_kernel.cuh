@@ -4,12 +4,12 @@
 //   u_s = y + delta_{s-1}                                   (stage input)
 //   k_s = -v d_z u_s  (FD4 + Kreiss-Oliger, Sec. 3.1, or FV WENO7, Sec. 3.2)
 //         - i [H(u_s), u_s]                                 (Eq. (eom), (ham))
-//   delta_1 = dt/2 k_1, delta_2 = dt/2 k_2, delta_3 = dt k_3,
-//   y <- y + (delta_1 + 2 delta_2 + delta_3) / 3 + dt/6 k_4   (classic RK4)
-// In the mixed path stage 4 writes delta_4 = dt k_4 like the other stages, and
-// a separate streaming kernel, apply_increment_kernel, forms
-//   dy = (delta_1 + 2 delta_2 + delta_3) / 3 + delta_4 / 6
-// in float, performs y <- y + dy in double and sums the v-moments of dy.
+//   delta_1 = dt/2 k_1, delta_2 = dt/2 k_2, delta_3 = dt k_3, delta_4 = dt k_4,
+// and a separate streaming kernel finishes the step (classic RK4):
+//   y <- y + (delta_1 + 2 delta_2 + delta_3) / 3 + delta_4 / 6
+// (FP64: apply_increment_fp64_kernel, into the other state buffer; mixed:
+// apply_increment_kernel forms the increment in float, adds it to y in double in
+// place and sums its v-moments).
 //
 // Work decomposition.  A CTA owns a contiguous range of z rows and all 2 nv
 // (species, v) columns, and marches along z with three warp roles:
@@ -128,10 +128,9 @@ __device__ __forceinline__ void vstore(T* p, const T (&in)[N]) {
 // Byte layout of one ring slot.  A slot carries R consecutive z rows: for each
 // array, the R rows of component plane q are contiguous ([q][r][v]) because
 // they are contiguous in global memory, so one bulk copy moves R rows of a
-// plane.  Window arrays belong to the leading rows i, center arrays (FP64
-// stage 4 only) to the rows i - lag.
+// plane.
 struct SlotLayout {
-  int y_off, din_off, yc_off, d1c_off, d2c_off, my_off, bytes;
+  int y_off, din_off, my_off, bytes;
 };
 
 template <int PREC>
@@ -140,19 +139,12 @@ __host__ __device__ inline SlotLayout slot_layout(int nv, int stage, int R) {
   using WinY = typename Prec<PREC>::WinY;
   SlotLayout L;
   const int row_w = 8 * nv * (int)sizeof(WinY) * R;
-  const int row_y = 8 * nv * (int)sizeof(double) * R;
   const int row_d = 8 * nv * (int)sizeof(Delta) * R;
   int off = 0;
   L.y_off = off;
   off += row_w;
   L.din_off = off;
   if (stage > 1) off += row_d;
-  L.yc_off = off;
-  if (stage == 4 && PREC == kFP64) off += row_y;
-  L.d1c_off = off;  // FP64 stage 4 only (the mixed stage 4 writes delta_4 instead)
-  if (stage == 4 && PREC == kFP64) off += row_d;
-  L.d2c_off = off;
-  if (stage == 4 && PREC == kFP64) off += row_d;
   L.my_off = off;
   if (PREC == kMIXED) off += 8 * (int)sizeof(double) * R;
   L.bytes = (off + 127) & ~127;
