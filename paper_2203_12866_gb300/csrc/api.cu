@@ -1,13 +1,13 @@
 // C ABI of the COSEnu GB300 engine (declared in include/cosenu.h).
 //
-// A handle owns one solver: the state (FP64 path: two ping-pong buffers, since
-// stage 4 reads the old state with a halo while writing the new one; mixed
-// path: one buffer plus its float copy, updated in place by the increment
-// kernel), the three RK4 stage increments, the per-z running moments of the
-// mixed path, and a small reduction scratch area.  cosenu_step() enqueues the
-// four fused stage kernels of each RK4 step (plus the increment kernel in the
-// mixed path) on the handle's stream; pairs of steps are replayed from a CUDA
-// graph when the stream allows capture.
+// A handle owns one solver: the state (FP64 path: two ping-pong buffers, the
+// increment kernel writing the new state into the other; mixed path: one buffer
+// plus its float copy, updated in place by the increment kernel), the four RK4
+// stage increments, the per-z running moments of the mixed path, and a small
+// reduction scratch area.  cosenu_step() enqueues the four fused stage kernels
+// of each RK4 step and the increment kernel (mixed: and the moment fold) on the
+// handle's stream; pairs of steps are replayed from a CUDA graph when the
+// stream allows capture.
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -526,12 +526,9 @@ cosenu_t create_common(int64_t nz, int32_t nv, double L, int scheme, int precisi
 // running FP64 moments.
 cudaError_t refresh_moments(cosenu_t h) {
   if (h->precision != COSENU_MIXED) return cudaSuccess;
-  const int64_t n = 8 * h->nz * (int64_t)h->nv;
-  y32_from_y_kernel<<<(int)std::min<int64_t>((n + 255) / 256, 8192), 256, 0, h->stream>>>(
-      h->y[h->ycur], h->y32[h->ycur], n);
-  ymoments_kernel<<<(int)std::min<int64_t>((h->nz + 7) / 8, 65535), 256, 0, h->stream>>>(
-      h->y[h->ycur], h->nz, h->nv, h->my, 8, h->vgrid);
-  g_launches.fetch_add(2, std::memory_order_relaxed);
+  y32_moments_kernel<<<(int)std::min<int64_t>((h->nz + 7) / 8, (int64_t)h->nsm * 8), 256, 0,
+                       h->stream>>>(h->y[0], h->y32[0], h->nz, h->nv, h->vtab, h->my);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
   return cudaGetLastError();
 }
 

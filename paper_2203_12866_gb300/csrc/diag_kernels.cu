@@ -48,13 +48,52 @@ __global__ void ymoments_kernel(const double* __restrict__ y, int64_t nz, int nv
   }
 }
 
-// Float copy of the state for the mixed path's stencil window:
-// y32 = round-to-nearest float of y (same conversion as the stage kernels).
-__global__ void y32_from_y_kernel(const double* __restrict__ y, float* __restrict__ y32,
-                                  int64_t n) {
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n;
-       e += (int64_t)gridDim.x * blockDim.x)
-    y32[e] = d2f_rn_int(y[e]);
+// Mixed path, after the state was replaced, in one pass over y: the float copy
+// y32 = round-to-nearest float of y (the stage kernels' conversion) and the
+// running FP64 v-moments my[z][k] (k < 6, as ymoments_kernel) with the beams and
+// weights of the handle's table vtab (v_j [nv], w_j [nv]).  One warp per z row,
+// lanes over v, then a butterfly: a fixed summation order.
+__global__ void y32_moments_kernel(const double* __restrict__ y, float* __restrict__ y32,
+                                   int64_t nz, int nv, const double* __restrict__ vtab,
+                                   double* __restrict__ my) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warps_total = (int64_t)gridDim.x * (blockDim.x >> 5);
+  for (int64_t z = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); z < nz;
+       z += warps_total) {
+    double m[6] = {0, 0, 0, 0, 0, 0};
+    for (int j = lane; j < nv; j += 32) {
+      const double v = vtab[j];
+      const double dv = vtab[nv + j];
+      double a[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int64_t e = ((int64_t)q * nz + z) * nv + j;
+        a[q] = y[e];
+        y32[e] = d2f_rn_int(a[q]);
+      }
+      const double d3 = (a[0] - a[1]) - (a[4] - a[5]);
+      const double dr = a[2] - a[6];
+      const double di = a[3] + a[7];
+      m[0] += dv * d3;
+      m[1] += dv * v * d3;
+      m[2] += dv * dr;
+      m[3] += dv * v * dr;
+      m[4] += dv * di;
+      m[5] += dv * v * di;
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m[k] += __shfl_xor_sync(0xffffffffu, m[k], o);
+    }
+    if (lane < 8) {
+      double val = 0.0;
+#pragma unroll
+      for (int k = 0; k < 6; ++k)
+        if (lane == k) val = m[k];
+      my[z * 8 + lane] = val;
+    }
+  }
 }
 
 // The step's float increment of four reals from the stage increments,

@@ -46,8 +46,9 @@ inline int apply_rows_per_chunk(int nv) { return kApplyGroups / (nv / 4); }
 
 __global__ void ymoments_kernel(const double* __restrict__ y, int64_t nz, int nv,
                                 double* __restrict__ out, int stride, int vgrid);
-__global__ void y32_from_y_kernel(const double* __restrict__ y, float* __restrict__ y32,
-                                  int64_t n);
+__global__ void y32_moments_kernel(const double* __restrict__ y, float* __restrict__ y32,
+                                   int64_t nz, int nv, const double* __restrict__ vtab,
+                                   double* __restrict__ my);
 __global__ void apply_increment_kernel(ApplySeg sg);
 __global__ void apply_increment_batch_kernel(const ApplySeg* __restrict__ segs,
                                              const int64_t* __restrict__ chunk_first, int nseg,
