@@ -59,3 +59,19 @@ def test_null_handle_calls_fail_cleanly(lib):
     assert lib.cosenu_steps_taken(None) == -1
     lib.cosenu_destroy(None)
     assert lib.cosenu_create_external(16, 32, 1.0, 0, 0, None, 0) is None
+
+
+def test_header_constants_match_binding():
+    """Every COSENU_* enumerator of include/cosenu.h has the same value in the
+    Python binding (the binding only marshals; a stale constant would pass a
+    different scheme, precision or status across the ABI)."""
+    import re
+    text = open(os.path.join(ROOT, "include", "cosenu.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    found = {}
+    for body in re.findall(r"enum\s*\{(.*?)\}", text, flags=re.S):
+        for name, val in re.findall(r"(COSENU_[A-Z0-9_]+)\s*=\s*(-?\d+)", body):
+            found[name] = int(val)
+    assert len(found) >= 16, found  # schemes, precisions, status codes, quadratures
+    for name, val in found.items():
+        assert getattr(binding, name) == val, name
