@@ -75,3 +75,41 @@ def test_header_constants_match_binding():
     assert len(found) >= 16, found  # schemes, precisions, status codes, quadratures
     for name, val in found.items():
         assert getattr(binding, name) == val, name
+
+
+def _ctype_of(decl):
+    """ctypes class expected for one C parameter or return declaration of the header."""
+    import ctypes
+    d = " ".join(decl.replace("const ", "").split())
+    if "*" in d or d.split()[0] in ("cosenu_t", "cosenu_batch_t", "cosenu_server_t"):
+        return "pointer"
+    base = d.split()[0]
+    return {"int64_t": ctypes.c_int64, "int32_t": ctypes.c_int32, "int": ctypes.c_int,
+            "size_t": ctypes.c_size_t, "double": ctypes.c_double, "uint64_t": ctypes.c_uint64,
+            "void": None}[base]
+
+
+def test_header_prototypes_match_binding(lib):
+    """Each function of include/cosenu.h is bound with the header's parameter count
+    and the same integer widths, floating types and pointer positions."""
+    import ctypes
+    text = open(os.path.join(ROOT, "include", "cosenu.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    protos = re.findall(r"([A-Za-z_][A-Za-z0-9_ \*]*?)\b(cosenu_\w+)\s*\(([^;{]*?)\)\s*;", text)
+    assert len(protos) >= 50
+    for ret, name, params in protos:
+        f = getattr(lib, name)
+        params = " ".join(params.split())
+        args = [] if params in ("", "void") else [p.strip() for p in params.split(",")]
+        assert len(f.argtypes) == len(args), name
+        for want, got in zip([_ctype_of(a) for a in args], f.argtypes):
+            if want == "pointer":
+                assert got is ctypes.c_void_p or got is ctypes.c_char_p or \
+                    issubclass(got, ctypes._Pointer), (name, got)
+            else:
+                assert got is want, (name, want, got)
+        want_ret = _ctype_of(ret.strip())
+        if want_ret == "pointer":
+            assert f.restype in (ctypes.c_void_p, ctypes.c_char_p), name
+        else:
+            assert f.restype is want_ret, (name, want_ret, f.restype)
