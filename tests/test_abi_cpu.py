@@ -113,3 +113,47 @@ def test_header_prototypes_match_binding(lib):
             assert f.restype in (ctypes.c_void_p, ctypes.c_char_p), name
         else:
             assert f.restype is want_ret, (name, want_ret, f.restype)
+
+
+def test_struct_layouts_match_binding(tmp_path):
+    """The ctypes mirrors of the header's structs have the C compiler's size and
+    field offsets (compiled with gcc against include/cosenu.h)."""
+    import ctypes
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = {
+        "cosenu_params": ["mu", "omega", "theta", ("lambda", "lambda_"), "ko_eps", "weno_eps", "dt"],
+        "cosenu_conserved_t": ["tr_nu", "tr_nubar", "M", "M_vac", "dP_max", "dP_mean", "step"],
+        "cosenu_batch_class": ["scheme", "precision", "nv", "members", "rows", "rows_per_slot",
+                               "ring", "grid", "smem", "occupancy", "concurrent", "kernel_ms"],
+        "cosenu_request": ["nz", "nv", "L", "scheme", "precision", "params", "nsteps", "state",
+                           "alpha", "sigma_nu", "sigma_nubar", "eps0", "seed", "out_state"],
+        "cosenu_result": ["status", "steps", "conserved", "t_submit", "t_admit", "t_done"],
+        "cosenu_server_stats": ["submitted", "admitted", "finished", "rounds", "steps", "queued",
+                                "running", "bytes_in_use", "peak_bytes", "budget"],
+    }
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "cosenu.h"', "int main(void) {"]
+    for s, fields in structs.items():
+        lines.append(f'  printf("{s} size %zu\\n", sizeof({s}));')
+        for f in fields:
+            c = f[0] if isinstance(f, tuple) else f
+            lines.append(f'  printf("{s} {c} %zu\\n", offsetof({s}, {c}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for ln in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n"):
+        if ln:
+            s, k, v = ln.split()
+            got[(s, k)] = int(v)
+    for s, fields in structs.items():
+        py = getattr(binding, s)
+        assert ctypes.sizeof(py) == got[(s, "size")], s
+        for f in fields:
+            c, p = (f if isinstance(f, tuple) else (f, f))
+            assert getattr(py, p).offset == got[(s, c)], (s, c)
