@@ -30,3 +30,17 @@ def test_oracle_does_not_use_the_package():
     pat = re.compile(r"paper_2203_12866_gb300|cosenu\.h\b|libcosenu\.so|stage_kernel|cosenu_device")
     for path in _sources(ORACLE, (".py", ".c", ".h")):
         assert not pat.search(open(path).read()), path
+
+
+def test_binding_fails_loudly_without_the_library(tmp_path):
+    """No fallback: a missing CUDA library is an error, not a silent CPU path."""
+    import subprocess
+    import sys
+    code = ("from paper_2203_12866_gb300 import binding\n"
+            "try:\n"
+            f"    binding.load({str(tmp_path / 'missing.so')!r})\n"
+            "except ImportError:\n"
+            "    print('raised')\n")
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
+                         check=True, timeout=120).stdout
+    assert out.strip() == "raised"
