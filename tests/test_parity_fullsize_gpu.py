@@ -55,7 +55,7 @@ def state_dev():
 
 @pytest.mark.parametrize("scheme,prec", [("fdko", "mixed"), ("fdko", "fp64"),
                                          ("weno7", "mixed"), ("weno7", "fp64"),
-                                         ("fdko3", "mixed")])
+                                         ("fdko3", "mixed"), ("fdko3", "fp64")])
 def test_fullsize_sampled_rows(state_dev, scheme, prec, oracle):
     sc = {"fdko": binding.COSENU_FDKO, "weno7": binding.COSENU_WENO7,
           "fdko3": binding.COSENU_FDKO3}[scheme]

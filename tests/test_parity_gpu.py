@@ -71,7 +71,7 @@ def test_mixed_ragged_tiles(scheme, nz, nv):
     u0 = inputs.random_state(nz, nv, seed=nz + nv, offdiag=0.05)
     got = run_gpu(u0, 0.2 * nz, SCHEMES[scheme], PRECS["mixed"], 6, mu=0.7, omega=0.2, theta=0.3)
     ref = run_oracle(u0, 0.2 * nz, SCHEMES[scheme], 6, mu=0.7, omega=0.2, theta=0.3)
-    assert max_abs(got, ref) <= 1e-5
+    assert rel_by_component(got, ref) <= MIXED_REL_TOL
 
 
 @pytest.mark.parametrize("scheme", ["fdko", "weno7", "fdko3"])
@@ -86,7 +86,7 @@ def test_tiny_periodic_grids(scheme, prec, nz):
     if prec == "fp64":
         assert max_abs(got, ref) <= FP64_TOL
     else:
-        assert max_abs(got, ref) <= 1e-5
+        assert rel_by_component(got, ref) <= MIXED_REL_TOL
 
 
 @pytest.mark.parametrize("scheme", ["fdko", "weno7", "fdko3"])
