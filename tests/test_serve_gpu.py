@@ -166,3 +166,58 @@ def test_poll_pending_then_done_and_destroy_cancels():
         srv.poll(t)  # collected already
     srv.submit(binding.make_request(256, 32, 20.0, FD, MIXED, nsteps=10 ** 6))
     srv.close()  # cancels the unfinished run and returns
+
+
+def _rel_by_component(got, ref):
+    worst = 0.0
+    for s in range(2):
+        for c in range(4):
+            scale = float(np.max(np.abs(ref[s, c])))
+            if scale > 0.0:
+                worst = max(worst, float(np.max(np.abs(got[s, c] - ref[s, c]))) / scale)
+    return worst
+
+
+def test_served_runs_match_oracle(oracle):
+    """Twelve runs served together -- each scheme in each precision, from a (smooth)
+    host state and from the device-built collective state -- against the FP64 oracle
+    stepping the same initial state: FP64 runs to 1e-12 (max |delta rho|), mixed
+    runs to 1e-5 relative per component, over 6-10 steps (half of the runs have a
+    vacuum term, whose off-diagonals reach a few percent).  The runs differ in
+    size, nv and parameters, so they share the batch's launches with runs of the
+    other precision and scheme."""
+    FD3 = binding.COSENU_FDKO3
+    runs = []
+    i = 0
+    for scheme in (FD, WENO, FD3):
+        for prec in (FP64, MIXED):
+            for host in (True, False):
+                nz, nv = 64 + 24 * i, (16, 32, 8)[i % 3]
+                L = 0.25 * nz
+                n = 6 + (i % 5)
+                params = dict(mu=1.0 + 0.1 * i, omega=0.3 * (i % 2), theta=0.2)
+                coll = dict(alpha=0.8 + 0.02 * i, sigma_nu=0.6, sigma_nubar=0.5, eps0=1e-6,
+                            seed=900 + i)
+                u0 = inputs.collective_state(nz, nv, **coll)
+                if host:  # a smooth host state that is not the collective recipe's
+                    z = np.arange(nz) / nz
+                    u0 = u0 * (1.0 + 1e-3 * np.sin(2 * np.pi * (z + 0.1 * i)))[None, None, :, None]
+                out = np.empty((2, 4, nz, nv))
+                req = binding.make_request(nz, nv, L, scheme, prec, nsteps=n,
+                                           state=u0 if host else None, out_state=out,
+                                           **({} if host else coll), **params)
+                runs.append((req, out, u0, (nz, nv, L, scheme, prec, n, params)))
+                i += 1
+    with binding.Server(1 << 30, round_steps=4) as srv:
+        tickets = [srv.submit(r) for r, *_ in runs]
+        results = [srv.wait(t, 60.0)[1] for t in tickets]
+    for (req, out, u0, (nz, nv, L, scheme, prec, n, params)), res in zip(runs, results):
+        assert res["status"] == binding.COSENU_OK and res["steps"] == n
+        p = oracle.params(nz, nv, L, scheme, **params)
+        ref = oracle.step(p, u0, n)
+        if prec == FP64:
+            err = float(np.max(np.abs(out - ref)))
+            assert err <= 1e-12, (nz, nv, scheme, prec, err)
+        else:
+            err = _rel_by_component(out, ref)
+            assert err <= 1e-5, (nz, nv, scheme, prec, err)
