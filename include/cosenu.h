@@ -196,6 +196,18 @@ int cosenu_sync(cosenu_t h);
  * Either output may be NULL.  Host buffers; waits. */
 int cosenu_moments(cosenu_t h, double* zavg, double* vmom);
 
+/* The per-z velocity moments from which the next stage kernel forms H_nunu,
+ * vmom[nz][6] in the order of cosenu_moments (host buffer; waits).
+ *   COSENU_MIXED: the double running sums D_n(y) the stage kernels read: set
+ *     from y by cosenu_set_state (and cosenu_set_quadrature), then advanced each
+ *     RK4 step by the v-sums of the step's float increment, which are summed in
+ *     float per (species, component, z) row.  Comparing them with
+ *     cosenu_moments' vmom, recomputed from y in double, measures how far the
+ *     running sums have drifted.
+ *   COSENU_FP64: the stage kernels sum the moments of each stage input in
+ *     double from the state itself, so this equals cosenu_moments' vmom. */
+int cosenu_running_moments(cosenu_t h, double* vmom);
+
 /* Diagnostics of the current state (waits). */
 int cosenu_conserved(cosenu_t h, cosenu_conserved_t* out);
 
@@ -426,6 +438,9 @@ const char* cosenu_server_last_error(cosenu_server_t s);
  * grid of length L, theta the vacuum mixing angle used for M_vac, and out_dev
  * a caller-owned device buffer of 8 doubles that receives
  *   tr_nu, tr_nubar, M[0], M[1], M[2], M_vac, dP_max, dP_mean.
+ * The sums use the midpoint bins (weight 2/nv per beam): with no handle there is
+ * no quadrature setting, so the results equal cosenu_conserved's only for
+ * handles on the default COSENU_MIDPOINT quadrature.
  * The work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
  * stream) and the call returns without waiting.
  *
@@ -442,8 +457,10 @@ const char* cosenu_server_last_error(cosenu_server_t s);
  *   - the grid may have at most 2^28 (z, v) cells (nz * nv <= 268435456);
  *     larger grids are rejected with COSENU_EINVAL and a message;
  *   - the first call on each device looks up the array's device address
- *     (cudaGetSymbolAddress, with that device current); make that first call
- *     before any stream capture;
+ *     (cudaGetSymbolAddress, with that device current) and keeps it for the
+ *     life of the process; make that first call before any stream capture.
+ *     The kept address does not survive a reset of the device's primary
+ *     context (cudaDeviceReset): do not call this function after one;
  *   - every call on a device shares the array: calls whose work overlaps on the
  *     GPU (different streams without ordering) race and give wrong results.
  *     Each call writes every partial it reads, so no clearing is needed between

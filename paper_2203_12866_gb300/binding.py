@@ -28,9 +28,9 @@ EXPORTS = (
     "cosenu_set_quadrature", "cosenu_velocities", "cosenu_set_params", "cosenu_get_params",
     "cosenu_set_stream", "cosenu_set_state", "cosenu_set_state_device",
     "cosenu_set_state_collective", "cosenu_get_state", "cosenu_get_rows", "cosenu_state_device",
-    "cosenu_step", "cosenu_sync", "cosenu_moments", "cosenu_conserved", "cosenu_dp_field",
-    "cosenu_spectrum", "cosenu_set_stage_timing", "cosenu_stage_times", "cosenu_steps_taken",
-    "cosenu_last_error", "cosenu_kernel_launches", "cosenu_batch_create", "cosenu_batch_destroy",
+    "cosenu_step", "cosenu_sync", "cosenu_moments", "cosenu_running_moments", "cosenu_conserved",
+    "cosenu_dp_field", "cosenu_spectrum", "cosenu_set_stage_timing", "cosenu_stage_times",
+    "cosenu_steps_taken", "cosenu_last_error", "cosenu_kernel_launches", "cosenu_batch_create", "cosenu_batch_destroy",
     "cosenu_batch_add", "cosenu_batch_remove", "cosenu_batch_size", "cosenu_batch_device_bytes",
     "cosenu_batch_step", "cosenu_batch_sync", "cosenu_batch_member", "cosenu_batch_tune",
     "cosenu_batch_classes", "cosenu_batch_class_info", "cosenu_batch_set_stage_timing",
@@ -127,6 +127,7 @@ def load(path: str = LIB_PATH):
         "cosenu_step": (ctypes.c_int, [vp, i64]),
         "cosenu_sync": (ctypes.c_int, [vp]),
         "cosenu_moments": (ctypes.c_int, [vp, dp, dp]),
+        "cosenu_running_moments": (ctypes.c_int, [vp, dp]),
         "cosenu_conserved": (ctypes.c_int, [vp, ctypes.POINTER(cosenu_conserved_t)]),
         "cosenu_dp_field": (ctypes.c_int, [vp, dp]),
         "cosenu_spectrum": (ctypes.c_int, [vp, i32, i32, i64, i64, dp]),
@@ -278,6 +279,13 @@ def cosenu_sync(h):
 
 def cosenu_moments(h, zavg=None, vmom=None):
     return _check(h, load().cosenu_moments(h, _dptr(zavg), _dptr(vmom)))
+
+
+def cosenu_running_moments(h, nz):
+    """The per-z moments [nz][6] the next stage kernel uses for H (see include/cosenu.h)."""
+    out = np.empty((nz, 6))
+    _check(h, load().cosenu_running_moments(h, _dptr(out)))
+    return out
 
 
 def cosenu_conserved(h):
@@ -572,6 +580,9 @@ class Solver:
         vmom = np.empty((self.nz, 6))
         cosenu_moments(self.h, zavg, vmom)
         return zavg, vmom
+
+    def running_moments(self):
+        return cosenu_running_moments(self.h, self.nz)
 
     def conserved(self):
         return cosenu_conserved(self.h)

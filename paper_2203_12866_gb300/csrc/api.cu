@@ -61,8 +61,8 @@ Layout make_layout(int64_t nz, int32_t nv, int precision) {
   L.d4 = off; off = align_up(off + n * dsz);
   L.my = off; off = align_up(off + (size_t)nz * 8 * sizeof(double));
   const size_t npm = precision == COSENU_MIXED ? (size_t)8 * nz : 0;
-  L.pmom = off; off = align_up(off + npm * sizeof(float2));
-  const size_t nwt = precision == COSENU_MIXED ? (size_t)2 * nv : 0;
+  L.pmom = off; off = align_up(off + npm * sizeof(float4));
+  const size_t nwt = precision == COSENU_MIXED ? (size_t)4 * nv : 0;
   L.wtab = off; off = align_up(off + nwt * sizeof(float));
   L.zavg = off; off = align_up(off + (size_t)8 * nv * sizeof(double));
   L.vtab = off; off = align_up(off + (size_t)2 * nv * sizeof(double));
@@ -432,13 +432,19 @@ void default_params(cosenu_t h) {
 // The beam velocities and weights of the handle's quadrature into its device
 // table (the stage kernels read them once per column).
 cudaError_t upload_vtab(cosenu_t h) {
-  std::vector<double> t((size_t)2 * h->nv);
-  std::vector<float> w((size_t)2 * h->nv);  // mixed: w_j and w_j v_j rounded to float
-  for (int j = 0; j < h->nv; ++j) {
-    t[j] = vgrid_v(j, h->nv, h->vgrid);
-    t[(size_t)h->nv + j] = vgrid_w(j, h->nv, h->vgrid);
-    w[j] = (float)t[(size_t)h->nv + j];
-    w[(size_t)h->nv + j] = (float)(t[(size_t)h->nv + j] * t[j]);
+  const size_t nv = (size_t)h->nv;
+  std::vector<double> t(2 * nv);
+  // mixed: w_j and w_j v_j (double) as float pairs hi + lo, hi = float(x), lo = float(x - hi)
+  std::vector<float> w(4 * nv);
+  for (size_t j = 0; j < nv; ++j) {
+    t[j] = vgrid_v((int)j, h->nv, h->vgrid);
+    t[nv + j] = vgrid_w((int)j, h->nv, h->vgrid);
+    const double x[2] = {t[nv + j], t[nv + j] * t[j]};
+    for (int k = 0; k < 2; ++k) {
+      const float hi = (float)x[k];
+      w[k * nv + j] = hi;
+      w[(2 + k) * nv + j] = (float)(x[k] - (double)hi);
+    }
   }
   cudaError_t e = cudaMemcpyAsync(h->vtab, t.data(), t.size() * sizeof(double),
                                   cudaMemcpyHostToDevice, h->stream);
@@ -508,7 +514,7 @@ cosenu_t create_common(int64_t nz, int32_t nv, double L, int scheme, int precisi
   h->d[2] = h->ws + h->lay.d3;
   h->d[3] = h->ws + h->lay.d4;
   if (precision == COSENU_MIXED) {
-    h->pmom = reinterpret_cast<float2*>(h->ws + h->lay.pmom);
+    h->pmom = reinterpret_cast<float4*>(h->ws + h->lay.pmom);
     h->wtab = reinterpret_cast<float*>(h->ws + h->lay.wtab);
   }
   h->my = reinterpret_cast<double*>(h->ws + h->lay.my);
@@ -819,6 +825,16 @@ int cosenu_moments(cosenu_t h, double* zavg, double* vmom) {
     CK(h, cudaMemcpy2DAsync(vmom, 6 * sizeof(double), dm, 8 * sizeof(double), 6 * sizeof(double),
                             (size_t)h->nz, cudaMemcpyDeviceToHost, h->stream));
   }
+  CK(h, cudaStreamSynchronize(h->stream));
+  return COSENU_OK;
+}
+
+int cosenu_running_moments(cosenu_t h, double* vmom) {
+  if (!h || !vmom) return fail(h, COSENU_EINVAL, "NULL argument");
+  if (h->precision != COSENU_MIXED) return cosenu_moments(h, nullptr, vmom);
+  // my is [nz][8] (6 used)
+  CK(h, cudaMemcpy2DAsync(vmom, 6 * sizeof(double), h->my, 8 * sizeof(double), 6 * sizeof(double),
+                          (size_t)h->nz, cudaMemcpyDeviceToHost, h->stream));
   CK(h, cudaStreamSynchronize(h->stream));
   return COSENU_OK;
 }

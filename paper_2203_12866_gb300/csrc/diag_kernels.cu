@@ -121,14 +121,58 @@ __device__ __forceinline__ bool apply4(double2* __restrict__ y, float4* __restri
   return is_finite_bits(a.x) && is_finite_bits(a.y) && is_finite_bits(b.x) && is_finite_bits(b.y);
 }
 
+// Error-free sum of two floats (Knuth's TwoSum): s + t == a + b exactly, with
+// s = fl(a + b).  Valid for any ordering of |a|, |b|; the explicit _rn
+// operations keep the compiler from contracting or reassociating them.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& t) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  t = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// sum_k w_k x_k of a float4 group as an unevaluated float pair hi + lo, with
+// the double weights w_k given as float pairs wh_k + wl_k: each product
+// wh_k x_k's rounding error is recovered exactly by an FMA and wl_k x_k added
+// to it, the three additions' errors are recovered by TwoSum, and the error
+// terms are summed in lo (relative error of hi + lo about 2^-44 of
+// sum_k |w_k x_k|).
+__device__ __forceinline__ float2 dot4_ff(float4 wh, float4 wl, float4 x) {
+  const float p0 = __fmul_rn(wh.x, x.x), p1 = __fmul_rn(wh.y, x.y);
+  const float p2 = __fmul_rn(wh.z, x.z), p3 = __fmul_rn(wh.w, x.w);
+  float lo = __fadd_rn(__fadd_rn(fmaf(wl.x, x.x, fmaf(wh.x, x.x, -p0)),
+                                 fmaf(wl.y, x.y, fmaf(wh.y, x.y, -p1))),
+                       __fadd_rn(fmaf(wl.z, x.z, fmaf(wh.z, x.z, -p2)),
+                                 fmaf(wl.w, x.w, fmaf(wh.w, x.w, -p3))));
+  float hi, t;
+  two_sum(p0, p1, hi, t);
+  lo = __fadd_rn(lo, t);
+  two_sum(hi, p2, hi, t);
+  lo = __fadd_rn(lo, t);
+  two_sum(hi, p3, hi, t);
+  return make_float2(hi, __fadd_rn(lo, t));
+}
+
+// (hi, lo) += (b.x, b.y) for float pairs: the high parts by TwoSum, the low
+// parts and the error plainly.
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float bhi, float blo) {
+  float t;
+  two_sum(hi, bhi, hi, t);
+  lo = __fadd_rn(lo, __fadd_rn(blo, t));
+}
+
 // Mixed path, end of an RK4 step, one chunk of plane-rows: y <- y + dy in
 // double and the float copy y32 <- round(y), in place, and the weighted v-sums
 // of dy of every plane-row of the chunk (pmom), from which the running FP64
 // v-moments of y advance (fold_moments_kernel).  dy is the float increment
-// formed per element; its v-sums are taken in a fixed order (each float4
-// group's four products, then the row's groups by lane and a butterfly), so
-// they depend only on the data and nv, not on the chunk or launch.
-__device__ __forceinline__ void apply_chunk(const ApplySeg& sg, int64_t ch, float2* sm) {
+// formed per element and added to y exactly (float to double); its v-sums
+// sum_j w_j dy_j, sum_j w_j v_j dy_j are carried as float pairs hi + lo
+// (products' and additions' rounding errors recovered exactly), so the running
+// double moments follow the moments of y to double precision instead of
+// accumulating float rounding step after step.  The sums are taken in a fixed
+// order (each float4 group's four products, then the row's groups by lane and a
+// butterfly), so they depend only on the data and nv, not on the chunk or
+// launch.
+__device__ __forceinline__ void apply_chunk(const ApplySeg& sg, int64_t ch, float4* sm) {
   const int L = sg.nv >> 2;  // float4 groups per plane-row
   const int64_t nprow = 8 * sg.nz;
   const int64_t pr0 = ch * sg.rows_per_chunk;
@@ -157,8 +201,10 @@ __device__ __forceinline__ void apply_chunk(const ApplySeg& sg, int64_t ch, floa
       const int v0 = (gg - r * L) * 4;
       const float4 w = *reinterpret_cast<const float4*>(sg.wtab + v0);
       const float4 wv = *reinterpret_cast<const float4*>(sg.wtab + sg.nv + v0);
-      sm[gg] = make_float2(((w.x * inc.x + w.y * inc.y) + w.z * inc.z) + w.w * inc.w,
-                           ((wv.x * inc.x + wv.y * inc.y) + wv.z * inc.z) + wv.w * inc.w);
+      const float4 wl = *reinterpret_cast<const float4*>(sg.wtab + 2 * sg.nv + v0);
+      const float4 wvl = *reinterpret_cast<const float4*>(sg.wtab + 3 * sg.nv + v0);
+      const float2 m0 = dot4_ff(w, wl, inc), m1 = dot4_ff(wv, wvl, inc);
+      sm[gg] = make_float4(m0.x, m0.y, m1.x, m1.y);
     };
     one(g, ia, rk4_increment(a1, a2, a3, a4));
     if (two) one(gb, ib, rk4_increment(b1, b2, b3, b4));
@@ -173,25 +219,27 @@ __device__ __forceinline__ void apply_chunk(const ApplySeg& sg, int64_t ch, floa
   const int sub = tid & (T - 1);
   for (int base = 0; base < sg.rows_per_chunk; base += kApplyThreads / T) {  // uniform trip count
     const int r = base + tid / T;
-    float s0 = 0.0f, s1 = 0.0f;
+    float h0 = 0.0f, l0 = 0.0f, h1 = 0.0f, l1 = 0.0f;
     if (r < nrow) {
       for (int l = sub; l < L; l += T) {
-        const float2 t = sm[r * L + l];
-        s0 += t.x;
-        s1 += t.y;
+        const float4 t = sm[r * L + l];
+        ff_add(h0, l0, t.x, t.y);
+        ff_add(h1, l1, t.z, t.w);
       }
     }
     for (int o = T >> 1; o > 0; o >>= 1) {
-      s0 += __shfl_xor_sync(0xffffffffu, s0, o);
-      s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+      const float a0 = __shfl_xor_sync(0xffffffffu, h0, o), b0 = __shfl_xor_sync(0xffffffffu, l0, o);
+      const float a1 = __shfl_xor_sync(0xffffffffu, h1, o), b1 = __shfl_xor_sync(0xffffffffu, l1, o);
+      ff_add(h0, l0, a0, b0);
+      ff_add(h1, l1, a1, b1);
     }
-    if (sub == 0 && r < nrow) sg.pmom[pr0 + r] = make_float2(s0, s1);
+    if (sub == 0 && r < nrow) sg.pmom[pr0 + r] = make_float4(h0, l0, h1, l1);
   }
   __syncthreads();  // sm is reused by the next chunk
 }
 
 __global__ void __launch_bounds__(kApplyThreads, 4) apply_increment_kernel(ApplySeg sg) {
-  __shared__ float2 sm[kApplyGroups];
+  __shared__ float4 sm[kApplyGroups];
   for (int64_t ch = blockIdx.x; ch < sg.nchunks; ch += gridDim.x) apply_chunk(sg, ch, sm);
 }
 
@@ -201,7 +249,7 @@ __global__ void __launch_bounds__(kApplyThreads, 4) apply_increment_kernel(Apply
 __global__ void __launch_bounds__(kApplyThreads, 4) apply_increment_batch_kernel(
     const ApplySeg* __restrict__ segs, const int64_t* __restrict__ chunk_first, int nseg,
     int64_t nchunks) {
-  __shared__ float2 sm[kApplyGroups];
+  __shared__ float4 sm[kApplyGroups];
   for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
     int lo = 0, hi = nseg - 1;  // last segment whose first chunk is <= ch
     while (lo < hi) {
@@ -282,14 +330,14 @@ __global__ void __launch_bounds__(256) apply_increment_fp64_batch_kernel(
 // my[z][k] += the z row's v-moments of the step's increment, from the eight
 // plane-row sums of (species, component): D3 = (ee - xx) - (ee - xx)bar,
 // Dr = Re - Re bar, Di = Im + Im bar (S - Sbar^*, Eq. (ham)), n = 0, 1; in double.
-__device__ __forceinline__ void fold_row(double* __restrict__ my, const float2* __restrict__ pmom,
+__device__ __forceinline__ void fold_row(double* __restrict__ my, const float4* __restrict__ pmom,
                                          int64_t nz, int64_t z) {
   double p0[8], p1[8];
 #pragma unroll
   for (int k = 0; k < 8; ++k) {
-    const float2 t = pmom[k * nz + z];
-    p0[k] = f2d_int(t.x);
-    p1[k] = f2d_int(t.y);
+    const float4 t = pmom[k * nz + z];  // (hi, lo) of both sums
+    p0[k] = f2d_int(t.x) + f2d_int(t.y);
+    p1[k] = f2d_int(t.z) + f2d_int(t.w);
   }
   double* m = my + z * 8;
   m[0] += (p0[0] - p0[1]) - (p0[4] - p0[5]);
@@ -300,7 +348,7 @@ __device__ __forceinline__ void fold_row(double* __restrict__ my, const float2* 
   m[5] += p1[3] + p1[7];
 }
 
-__global__ void fold_moments_kernel(double* __restrict__ my, const float2* __restrict__ pmom,
+__global__ void fold_moments_kernel(double* __restrict__ my, const float4* __restrict__ pmom,
                                     int64_t nz) {
   for (int64_t z = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; z < nz;
        z += (int64_t)gridDim.x * blockDim.x)

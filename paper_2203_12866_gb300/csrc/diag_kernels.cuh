@@ -22,8 +22,10 @@ struct ApplySeg {
   double* y;
   float* y32;
   const float* d[4];    // the four stage increments
-  float2* pmom;         // [8 nz] per plane-row: sum_j w_j dy_j, sum_j w_j v_j dy_j
-  const float* wtab;    // [2][nv]: w_j, w_j v_j of the quadrature (float)
+  float4* pmom;         // [8 nz] per plane-row: sum_j w_j dy_j, sum_j w_j v_j dy_j as
+                        // float pairs (hi, lo, hi, lo)
+  const float* wtab;    // [4][nv]: the double weights w_j, w_j v_j of the quadrature as
+                        // float pairs: high parts [0], [1], low parts [2], [3]
   double* my;           // [nz][8] running FP64 v-moments of y
   int64_t nz;
   int32_t nv;
@@ -63,7 +65,7 @@ __global__ void apply_increment_fp64_kernel(const double* __restrict__ y_in,
 __global__ void apply_increment_fp64_batch_kernel(const ApplySeg64* __restrict__ segs,
                                                   const int64_t* __restrict__ chunk_first,
                                                   int nseg, int64_t nchunks);
-__global__ void fold_moments_kernel(double* __restrict__ my, const float2* __restrict__ pmom,
+__global__ void fold_moments_kernel(double* __restrict__ my, const float4* __restrict__ pmom,
                                     int64_t nz);
 __global__ void fold_moments_batch_kernel(const ApplySeg* __restrict__ segs,
                                           const int64_t* __restrict__ block_first, int nseg,

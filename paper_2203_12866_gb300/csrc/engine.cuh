@@ -52,8 +52,8 @@ struct cosenu_s {
   int ycur = 0;
   void* d[4] = {nullptr, nullptr, nullptr, nullptr};  // delta_1..3 (mixed: and delta_4)
   double* my = nullptr;
-  float2* pmom = nullptr;  // mixed: weighted v-sums of the step's increment per plane-row
-  float* wtab = nullptr;   // mixed: quadrature weights w_j and w_j v_j in float, [2][nv]
+  float4* pmom = nullptr;  // mixed: weighted v-sums of the step's increment per plane-row (float pairs)
+  float* wtab = nullptr;   // mixed: w_j and w_j v_j as float pairs (hi [2][nv], lo [2][nv])
   double* vtab = nullptr;  // beam velocities [nv] and quadrature weights [nv]
   uint32_t* err = nullptr;
   cosenu::StageCfg cfg[5];
