@@ -53,3 +53,18 @@ def test_bounded_wait_gives_up_and_raises_abort(tmp_path):
     assert err == 2  # the timeout bit (kErrTimeout), nothing else
     assert 0 < waited1 < limit  # warp 1 left on the abort flag, before its own limit
     assert out[5] == "usable"
+
+
+def test_fma_peaks(tmp_path):
+    """Measured FMA throughput of the GPU (FP64 and FP32), the ALU peaks against
+    which the FP64 stage kernels (and the instruction-bound mixed WENO7 kernels)
+    are reported.  From the unit counts at 2.07 GHz: FP64 1.26 TFLOP/s (152 SMs x 2
+    FP64 FMA lanes per clock x 2 flops), FP32 80.5 TFLOP/s (152 SMs x 128 lanes x 2)."""
+    exe = str(tmp_path / "fma_peak")
+    subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-std=c++17",
+                    os.path.join(HERE, "gpu_probes", "fma_peak.cu"), "-o", exe], check=True)
+    out = subprocess.run([exe], check=True, capture_output=True, text=True,
+                         timeout=120).stdout.split()
+    fp64, fp32, sms = float(out[1]), float(out[3]), int(out[5])
+    print(f"FMA peaks: fp64 {fp64:.3f} TFLOP/s, fp32 {fp32:.2f} TFLOP/s on {sms} SMs")
+    assert 0.5 < fp64 < 2.0 and 30.0 < fp32 < 120.0
