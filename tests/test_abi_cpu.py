@@ -157,3 +157,21 @@ def test_struct_layouts_match_binding(tmp_path):
         for f in fields:
             c, p = (f if isinstance(f, tuple) else (f, f))
             assert getattr(py, p).offset == got[(s, c)], (s, c)
+
+
+@pytest.mark.parametrize("y,nz,nv,L,out", [(None, 16, 8, 1.0, 64), (64, 16, 8, 1.0, None),
+                                           (64, 0, 8, 1.0, 64), (64, 16, 0, 1.0, 64),
+                                           (64, 16, 8, 0.0, 64), (64, 16, 8, -2.0, 64)])
+def test_conserved_noalloc_rejects_bad_arguments_without_device_work(lib, y, nz, nv, L, out):
+    """The argument checks return before any CUDA call (the pointers are never
+    dereferenced on this path, so placeholder addresses are safe)."""
+    rc = lib.cosenu_conserved_noalloc(y, nz, nv, L, 0.0, out, None)
+    assert rc == binding.COSENU_EINVAL
+    assert "NULL pointer, nz < 1, nv < 1 or L <= 0" in binding.cosenu_last_error(None)
+
+
+def test_conserved_noalloc_rejects_grids_beyond_its_static_scratch(lib):
+    rc = lib.cosenu_conserved_noalloc(64, (1 << 28) // 256 + 1, 256, 1.0, 0.0, 64, None)
+    assert rc == binding.COSENU_EINVAL
+    assert "exceeds the static scratch limit" in binding.cosenu_last_error(None)
+    assert "268435456" in binding.cosenu_last_error(None)
