@@ -454,25 +454,51 @@ def serve_trace(b, trace, budget, rate_scale=1.0, max_running=0, precision=None)
 
 
 def run_serving(args):
-    """Continuous batching on a Poisson trace, a second trace at 70% of the measured
-    capacity, and the first trace served one run at a time in FP64."""
+    """Continuous batching on the serving trace.  Leads with arrivals stretched to 70%
+    of the capacity the loop measures on the trace's own burst of arrivals (50 per
+    second: all runs resident almost at once, so that leg's p50/p99 are close to its
+    makespan).  On the same 70% arrivals, the runs served one at a time, each at its
+    own precision (the same accuracy), and all in FP64 (the plain single-instance
+    path)."""
     from paper_2203_12866_gb300 import binding as b
     from paper_2203_12866_gb300 import inputs
 
     trace = inputs.serving_trace(args.serve_requests, args.serve_rate,
                                  step_scale=args.serve_step_scale)
     budget = 64 << 30
+    burst = serve_trace(b, trace, budget)  # the capacity measurement
+    cap = burst["completed_per_s"]
+    scale = 0.7 * cap / args.serve_rate  # arrival times stretched to 70% of capacity
     out = {"workload": SERVE_WORKLOAD, "rate_per_s": args.serve_rate,
            "step_scale": args.serve_step_scale,
            "steps_range": [min(r["nsteps"] for r in trace), max(r["nsteps"] for r in trace)],
            "cell_updates": sum(2 * r["nz"] * r["nv"] * r["nsteps"] for r in trace)}
-    out["batched"] = serve_trace(b, trace, budget)
-    cap = out["batched"]["completed_per_s"]
-    scale = 0.7 * cap / args.serve_rate  # arrival times stretched to 70% of capacity
     out["batched_70pct"] = serve_trace(b, trace, budget, rate_scale=scale)
-    if args.serve_fp64_baseline:
-        out["fp64_one_at_a_time"] = serve_trace(b, trace, budget, max_running=1,
-                                                precision=b.COSENU_FP64)
+    out["batched_burst"] = burst
+    if args.serve_baselines:
+        out["one_at_a_time_70pct"] = serve_trace(b, trace, budget, rate_scale=scale,
+                                                 max_running=1)
+        out["fp64_one_at_a_time_70pct"] = serve_trace(b, trace, budget, rate_scale=scale,
+                                                      max_running=1, precision=b.COSENU_FP64)
+    return out
+
+
+def summary(value, ms_step, roofline, variants, small, batched, serving):
+    """The line's key figures in a few hundred characters, placed last."""
+    r3 = lambda x: None if x is None else float(f"{x:.4g}")  # noqa: E731
+    out = {"ms_per_step": r3(ms_step), "value": r3(value), "step_hbm_frac": r3(roofline["step_frac"]),
+           "dominant_frac": r3(roofline["frac"])}
+    if variants:
+        out["variants_ms_per_step"] = {k: r3(v["ms_per_step"]) for k, v in variants.items()}
+    if small:
+        out["small_us_per_step"] = {k: r3(v["us_per_step"]) for k, v in small.items()}
+    if batched:
+        out["batched"] = {"ms_per_step": r3(batched["ms_per_step"]), "value": r3(batched["value"]),
+                          "hbm_frac": r3(batched["hbm"]["frac"]),
+                          "launches_per_step": r3(batched["gpu_launches"] / batched["steps"])}
+    if serving:
+        out["serving_p50_p99_s"] = {k: [r3(v["p50_s"]), r3(v["p99_s"])] for k, v in serving.items()
+                                    if isinstance(v, dict) and "p50_s" in v}
     return out
 
 
@@ -614,6 +640,7 @@ def run_ours(args, world, rank, local):
             "serving": serving,
             "conserved_after": {"tr_nu": cons["tr_nu"], "M": list(cons["M"]),
                                 "dP_max": cons["dP_max"]},
+            "summary": summary(value, ms_step, roofline, variants, small, batched, serving),
         }
         print(json.dumps(line), flush=True)
 
@@ -638,10 +665,10 @@ def main():
     ap.add_argument("--no-serving", dest="serving", action="store_false")
     ap.add_argument("--serve-requests", type=int, default=32)
     ap.add_argument("--serve-rate", type=float, default=50.0)
-    ap.add_argument("--serve-step-scale", type=float, default=0.05,
+    ap.add_argument("--serve-step-scale", type=float, default=0.1,
                     help="fraction of each run's t_final simulated (1 = the full trace)")
-    ap.add_argument("--no-serve-fp64-baseline", dest="serve_fp64_baseline",
-                    action="store_false")
+    ap.add_argument("--no-serve-baselines", dest="serve_baselines", action="store_false",
+                    help="skip the one-at-a-time legs")
     ap.add_argument("--nz", type=int, default=NZ_FULL,
                     help="z cells (smaller values only for profiling captures)")
     args = ap.parse_args()
