@@ -267,9 +267,19 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return r;
 }
 
+// float arithmetic with the rounding written out: products and sums are never
+// contracted into fused multiply-adds or reassociated, so a value computed by
+// these depends only on its inputs, not on the surrounding code.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
 // float: fast reciprocals for the weights (the mixed path's weights need no more).
 // The face from its differences e_-3..e_2, g_-3..g_1 and the third-difference
-// terms T_r = (781/3) c_r^2 + eps (T_0 from h_0 .. T_3 from h_-3).
+// terms T_r = (781/3) c_r^2 + eps (T_0 from h_0 .. T_3 from h_-3).  Every
+// operation is an explicit rounding (see mul_rn), so two faces evaluated in one
+// pass from shared differences are each bitwise what a lone evaluation gives.
 __device__ __forceinline__ float weno7_face_core(float f0, float em3, float em2, float em1,
                                                  float e0, float e1, float e2, float gm3,
                                                  float gm2, float gm1, float g0, float g1,
@@ -277,63 +287,57 @@ __device__ __forceinline__ float weno7_face_core(float f0, float em3, float em2,
   constexpr float s1 = 2.5819888974716112f;  // sqrt(20/3)
   constexpr float s2 = 16.124515496597099f;  // sqrt(260)
   // sqrt(20/3) a_r and sqrt(260) b_r
-  const float a0 = (11.0f * s1) * e0 - (7.0f * s1) * e1 + (2.0f * s1) * e2;
-  const float a1 = (2.0f * s1) * em1 + (5.0f * s1) * e0 - s1 * e1;
-  const float a2 = -s1 * em2 + (5.0f * s1) * em1 + (2.0f * s1) * e0;
-  const float a3 = (2.0f * s1) * em3 - (7.0f * s1) * em2 + (11.0f * s1) * em1;
-  const float b0 = (2.0f * s2) * g0 - s2 * g1;
-  const float b12 = s2 * gm1;
-  const float b3 = (2.0f * s2) * gm2 - s2 * gm3;
+  const float a0 = fma_rn(2.0f * s1, e2, fma_rn(-7.0f * s1, e1, mul_rn(11.0f * s1, e0)));
+  const float a1 = fma_rn(-s1, e1, fma_rn(5.0f * s1, e0, mul_rn(2.0f * s1, em1)));
+  const float a2 = fma_rn(2.0f * s1, e0, fma_rn(5.0f * s1, em1, mul_rn(-s1, em2)));
+  const float a3 = fma_rn(11.0f * s1, em1, fma_rn(-7.0f * s1, em2, mul_rn(2.0f * s1, em3)));
+  const float b0 = fma_rn(-s2, g1, mul_rn(2.0f * s2, g0));
+  const float b12 = mul_rn(s2, gm1);
+  const float b3 = fma_rn(-s2, gm3, mul_rn(2.0f * s2, gm2));
   // SI_r + eps
-  const float t0 = fmaf(a0, a0, fmaf(b0, b0, T0));
-  const float t1 = fmaf(a1, a1, fmaf(b12, b12, T1));
-  const float t2 = fmaf(a2, a2, fmaf(b12, b12, T2));
-  const float t3 = fmaf(a3, a3, fmaf(b3, b3, T3));
+  const float t0 = fma_rn(a0, a0, fma_rn(b0, b0, T0));
+  const float t1 = fma_rn(a1, a1, fma_rn(b12, b12, T1));
+  const float t2 = fma_rn(a2, a2, fma_rn(b12, b12, T2));
+  const float t3 = fma_rn(a3, a3, fma_rn(b3, b3, T3));
   // d_r delta_r: the linear weights 4/35, 18/35, 12/35, 1/35 folded into the
   // candidates' coefficients
-  const float dd0 = (3.0f / 35.0f) * e0 - (4.0f / 105.0f) * e1 + (1.0f / 105.0f) * e2;
-  const float dd1 = (3.0f / 70.0f) * em1 + (9.0f / 35.0f) * e0 - (3.0f / 70.0f) * e1;
-  const float dd2 = -(1.0f / 35.0f) * em2 + (4.0f / 35.0f) * em1 + (3.0f / 35.0f) * e0;
-  const float dd3 = (1.0f / 140.0f) * em3 - (1.0f / 42.0f) * em2 + (13.0f / 420.0f) * em1;
+  const float dd0 = fma_rn(1.0f / 105.0f, e2, fma_rn(-4.0f / 105.0f, e1, mul_rn(3.0f / 35.0f, e0)));
+  const float dd1 = fma_rn(-3.0f / 70.0f, e1, fma_rn(9.0f / 35.0f, e0, mul_rn(3.0f / 70.0f, em1)));
+  const float dd2 = fma_rn(3.0f / 35.0f, e0, fma_rn(4.0f / 35.0f, em1, mul_rn(-1.0f / 35.0f, em2)));
+  const float dd3 =
+      fma_rn(13.0f / 420.0f, em1, fma_rn(-1.0f / 42.0f, em2, mul_rn(1.0f / 140.0f, em3)));
   // 1 / (SI_r + eps)^2; the nonlinear weights are d_r times these
-  const float q0 = rcp_approx(t0 * t0), q1 = rcp_approx(t1 * t1);
-  const float q2 = rcp_approx(t2 * t2), q3 = rcp_approx(t3 * t3);
-  const float num = q0 * dd0 + q1 * dd1 + q2 * dd2 + q3 * dd3;
-  const float ws = (4.0f / 35.0f) * q0 + (18.0f / 35.0f) * q1 + (12.0f / 35.0f) * q2 +
-                   (1.0f / 35.0f) * q3;
-  return f0 + __fdividef(num, ws);
-}
-
-// The value unchanged, opaque to the optimiser: keeps two evaluations of
-// weno7_face_core from sharing products (whose fused multiply-adds would then
-// round differently), so a face is bitwise the same whichever of the pair it is.
-__device__ __forceinline__ float opaque(float x) {
-  asm volatile("" : "+f"(x));
-  return x;
+  const float q0 = rcp_approx(mul_rn(t0, t0)), q1 = rcp_approx(mul_rn(t1, t1));
+  const float q2 = rcp_approx(mul_rn(t2, t2)), q3 = rcp_approx(mul_rn(t3, t3));
+  const float num = fma_rn(q3, dd3, fma_rn(q2, dd2, fma_rn(q1, dd1, mul_rn(q0, dd0))));
+  const float ws = fma_rn(1.0f / 35.0f, q3,
+                          fma_rn(12.0f / 35.0f, q2, fma_rn(18.0f / 35.0f, q1,
+                                                           mul_rn(4.0f / 35.0f, q0))));
+  return add_rn(f0, mul_rn(num, rcp_approx(ws)));
 }
 
 // Two adjacent float faces from eight values x_0..x_7: P from x_0..x_6 (f_0 =
 // x_3) and Q from x_1..x_7 (f_0 = x_4).  The differences and the third-difference
-// terms of the overlapping stencils are formed once.
+// terms of the overlapping stencils are formed once (each is the same rounded
+// value whichever face uses it), so P and Q are bitwise the faces a lone
+// evaluation of their seven values gives.
 __device__ __forceinline__ void weno7_face_pair(float x0, float x1, float x2, float x3, float x4,
                                                 float x5, float x6, float x7, float eps,
                                                 float& P, float& Q) {
   constexpr float c3 = 781.0f / 3.0f;
-  const float e0 = x1 - x0, e1 = x2 - x1, e2 = x3 - x2, e3 = x4 - x3, e4 = x5 - x4,
-              e5 = x6 - x5, e6 = x7 - x6;
-  const float g0 = e1 - e0, g1 = e2 - e1, g2 = e3 - e2, g3 = e4 - e3, g4 = e5 - e4, g5 = e6 - e5;
-  const float h0 = g1 - g0, h1 = g2 - g1, h2 = g3 - g2, h3 = g4 - g3, h4 = g5 - g4;
-  const float T0 = fmaf(c3 * h0, h0, eps), T1 = fmaf(c3 * h1, h1, eps),
-              T2 = fmaf(c3 * h2, h2, eps), T3 = fmaf(c3 * h3, h3, eps),
-              T4 = fmaf(c3 * h4, h4, eps);
+  const float e0 = sub_rn(x1, x0), e1 = sub_rn(x2, x1), e2 = sub_rn(x3, x2), e3 = sub_rn(x4, x3),
+              e4 = sub_rn(x5, x4), e5 = sub_rn(x6, x5), e6 = sub_rn(x7, x6);
+  const float g0 = sub_rn(e1, e0), g1 = sub_rn(e2, e1), g2 = sub_rn(e3, e2), g3 = sub_rn(e4, e3),
+              g4 = sub_rn(e5, e4), g5 = sub_rn(e6, e5);
+  const float h0 = sub_rn(g1, g0), h1 = sub_rn(g2, g1), h2 = sub_rn(g3, g2), h3 = sub_rn(g4, g3),
+              h4 = sub_rn(g5, g4);
+  const float T0 = fma_rn(mul_rn(c3, h0), h0, eps), T1 = fma_rn(mul_rn(c3, h1), h1, eps),
+              T2 = fma_rn(mul_rn(c3, h2), h2, eps), T3 = fma_rn(mul_rn(c3, h3), h3, eps),
+              T4 = fma_rn(mul_rn(c3, h4), h4, eps);
   // local indices: e_-3 .. e_2 = e[b] .. e[b+5], g_-3 .. g_1 = g[b] .. g[b+4],
   // h_-3 .. h_0 = h[b] .. h[b+3] for the stencil starting at x_b
-  P = weno7_face_core(opaque(x3), opaque(e0), opaque(e1), opaque(e2), opaque(e3), opaque(e4),
-                      opaque(e5), opaque(g0), opaque(g1), opaque(g2), opaque(g3), opaque(g4),
-                      opaque(T3), opaque(T2), opaque(T1), opaque(T0));
-  Q = weno7_face_core(opaque(x4), opaque(e1), opaque(e2), opaque(e3), opaque(e4), opaque(e5),
-                      opaque(e6), opaque(g1), opaque(g2), opaque(g3), opaque(g4), opaque(g5),
-                      opaque(T4), opaque(T3), opaque(T2), opaque(T1));
+  P = weno7_face_core(x3, e0, e1, e2, e3, e4, e5, g0, g1, g2, g3, g4, T3, T2, T1, T0);
+  Q = weno7_face_core(x4, e1, e2, e3, e4, e5, e6, g1, g2, g3, g4, g5, T4, T3, T2, T1);
 }
 
 // ---------------------------------------------------------------- the kernel
