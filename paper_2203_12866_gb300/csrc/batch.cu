@@ -132,8 +132,10 @@ bool versions_current(const cosenu_batch_t b) {
   return true;
 }
 
-// Work items of one class stage: about factor x SMs x resident CTAs of them,
-// at least kMinRowsPerCta rows each (cfg.rows: the target rows per item).
+// Work items of one class stage: at most factor x SMs x resident CTAs of them
+// (a whole number of waves of resident CTAs, so no last wave runs a few items
+// on an otherwise idle GPU), at least kMinRowsPerCta rows each (cfg.rows: the
+// rows per item; each member is cut into ceil(nz / rows) near-equal ranges).
 void shape_stage(cosenu_batch_t b, ClassPlan& c, int s) {
   const Shape sh = c.shape[s];
   const RingChoice& rc = c.choices[s][sh.choice];
@@ -145,10 +147,24 @@ void shape_stage(cosenu_batch_t b, ClassPlan& c, int s) {
   cf.smem = rc.smem;
   c.occ[s] = rc.occ;
   const int64_t target = std::max<int64_t>(1, (int64_t)b->nsm * rc.occ * sh.gridf);
-  cf.rows = std::max<int64_t>(kMinRowsPerCta, (c.rows + target - 1) / target);
-  int64_t items = 0;
-  for (int mi : c.members) items += (b->members[mi]->nz + cf.rows - 1) / cf.rows;
-  cf.grid = (int)items;
+  auto items_for = [&](int64_t rows) {
+    int64_t n = 0;
+    for (int mi : c.members) n += (b->members[mi]->nz + rows - 1) / rows;
+    return n;
+  };
+  int64_t lo = std::max<int64_t>(kMinRowsPerCta, (c.rows + target - 1) / target);
+  if (items_for(lo) > target) {
+    // the smallest row count whose items fit the waves (items fall as rows grow;
+    // with more members than target, one item per member is the floor)
+    int64_t hi = lo;
+    for (int mi : c.members) hi = std::max<int64_t>(hi, b->members[mi]->nz);
+    while (lo < hi) {
+      const int64_t mid = lo + (hi - lo) / 2;
+      if (items_for(mid) > target) lo = mid + 1; else hi = mid;
+    }
+  }
+  cf.rows = lo;
+  cf.grid = (int)items_for(cf.rows);
 }
 
 // Host image of the launch tables; offsets are recorded in the class plans.

@@ -350,13 +350,16 @@ __host__ __device__ constexpr int stage_max_threads() {
 }
 
 // Minimum resident CTAs per SM the compiler is told to allow for.  The mixed
-// FD4+KO kernels are left to the compiler's own register budget (two 320-thread
-// CTAs per SM at 96 registers, which streams fastest); the FP64 and WENO7
-// kernels run one CTA per SM and are faster with the whole per-CTA budget
-// (measured: mixed WENO7 stage 1 15.5 -> 11.8 ms, FP64 FD4+KO 335 -> 331 ms per step).
-template <int SCHEME, int PREC, int STAGE>
+// FD4+KO kernels stream fastest as two 320-thread CTAs per SM at 96 registers:
+// the single-grid form gets there by itself, the batched form (which loads its
+// argument block from memory) is held to it (it would otherwise take 113-117
+// registers, leaving fewer small CTAs resident: 256-grid batched step 32.0 ->
+// 31.7 ms).  The FP64 and WENO7 kernels run one CTA per SM and are faster with
+// the whole per-CTA budget (measured: mixed WENO7 stage 1 15.5 -> 11.8 ms, FP64
+// FD4+KO 335 -> 331 ms per step).
+template <int SCHEME, int PREC, int STAGE, bool BATCHED>
 __host__ __device__ constexpr int stage_min_blocks() {
-  return (SCHEME != kWENO7 && PREC == kMIXED) ? 0 : 1;
+  return (SCHEME != kWENO7 && PREC == kMIXED) ? (BATCHED ? 2 : 0) : 1;
 }
 
 // Shared memory of a stage kernel besides its ring slots.
@@ -388,7 +391,7 @@ struct BatchTable {
 // as in a single-grid launch.
 template <int SCHEME, int PREC, int STAGE, bool BATCHED>
 __global__ void __launch_bounds__(stage_max_threads<SCHEME, PREC, STAGE>(),
-                                  stage_min_blocks<SCHEME, PREC, STAGE>())
+                                  stage_min_blocks<SCHEME, PREC, STAGE, BATCHED>())
     rk4_stage_kernel(const StageArgs a, const BatchTable bt) {
   if constexpr (BATCHED) {
     const WorkItem w = bt.items[blockIdx.x];
