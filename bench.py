@@ -67,8 +67,18 @@ FP64_FLOPS_PER_CELL = {"fdko": (81, 85, 85, 85, 32), "weno7": (531, 535, 535, 53
 SCHEMES = {"fdko": 0, "weno7": 1}
 PRECS = {"fp64": 0, "mixed": 1}
 NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal (the measured copy bandwidth is the peak used)
-# 152 SMs x 2 FP64 FMA lanes per clock x 2 flops x 2.07 GHz (nominal 1.25 TFLOP/s)
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def fp64_peak():
+    """FP64 FMA peak measured by the FMA probe (profiles/fma_peak.json), else the
+    unit-count figure 152 SMs x 2 FP64 FMA lanes x 2 flops x 2.07 GHz."""
+    path = os.path.join(ROOT, "profiles", "fma_peak.json")
+    if os.path.exists(path):
+        return float(json.load(open(path))["fp64_tflops"]), "measured (FMA probe)"
+    return 152 * 2 * 2 * 2.07e9 / 1e12, "unit counts"
+
+
+FP64_PEAK_TFLOPS, FP64_PEAK_KIND = fp64_peak()
 
 
 def peaks():
@@ -607,6 +617,8 @@ def run_ours(args, world, rank, local):
                     rec["bound"] = "alu"
                     rec["fp64_tflops"] = fl / (vms / k * 1e-3) / 1e12
                     rec["fp64_alu_frac"] = rec["fp64_tflops"] / FP64_PEAK_TFLOPS
+                    rec["fp64_peak_tflops"] = FP64_PEAK_TFLOPS
+                    rec["fp64_peak_kind"] = FP64_PEAK_KIND
                 variants[f"{sc}_{pr}"] = rec
     del state
     torch.cuda.empty_cache()
