@@ -154,8 +154,8 @@ __host__ __device__ inline SlotLayout slot_layout(int nv, int stage, int R) {
 // Shared memory besides the ring.  Acc is the type of the moment partials.
 //   mbarriers: full[kMaxRing] empty[kMaxRing] part[kMomSlots] mom[kMomSlots]
 //   flags (abort), partials [kMomSlots][NW consumer warps][8] Acc, finished
-//   moments [kMomSlots][8] Acc (FP64: the Hamiltonian's coefficients
-//   [kMomSlots][2 species][8]), running moments of y (mixed) [kMomSlots][8] double.
+//   moments or the Hamiltonian's coefficients [kMomSlots][2 species][8] Acc,
+//   running moments of y (mixed) [kMomSlots][8] double.
 template <int PREC, int NW>
 struct SmemHeader {
   using Acc = typename Prec<PREC>::Real;
@@ -165,8 +165,7 @@ struct SmemHeader {
   static constexpr int kPart = ((kFlags + 64) + 127) & ~127;
   static constexpr int kPartBytes = kMomSlots * NW * 8 * (int)sizeof(Acc);
   static constexpr int kMomf = kPart + kPartBytes;
-  // FP64: the Hamiltonian's coefficients of both species, [kMomSlots][2][8]
-  static constexpr int kMyRing = kMomf + kMomSlots * (PREC == kFP64 ? 16 : 8) * (int)sizeof(Acc);
+  static constexpr int kMyRing = kMomf + kMomSlots * 16 * (int)sizeof(Acc);
   static constexpr int kBytes = ((kMyRing + kMomSlots * 8 * 8) + 127) & ~127;
 };
 
