@@ -779,7 +779,8 @@ int cosenu_step(cosenu_t h, int64_t nsteps) {
     }
     for (; left >= 2; left -= 2) {
       CK(h, cudaGraphLaunch(h->graph, h->stream));
-      g_launches.fetch_add(h->precision == COSENU_MIXED ? 10 : 8, std::memory_order_relaxed);
+      // two steps of 6 (mixed: stages, increment, moment fold) or 5 (FP64) kernels
+      g_launches.fetch_add(h->precision == COSENU_MIXED ? 12 : 10, std::memory_order_relaxed);
     }
   }
   for (; left > 0; --left) {

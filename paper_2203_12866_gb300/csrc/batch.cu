@@ -589,7 +589,8 @@ int cosenu_batch_add(cosenu_batch_t b, int64_t nz, int32_t nv, double L, int sch
   if (dev != b->device) return bfail(b, COSENU_EINVAL, "the current device is not the batch's");
   cosenu_t h = create_member(nz, nv, L, scheme, precision, b->stream);
   if (!h) return bfail(b, COSENU_EINVAL, std::string("member: ") + cosenu_last_error(nullptr));
-  h->ycur = b->parity;  // zero state: either buffer will do
+  // zero state: either FP64 buffer will do (mixed members have one state buffer)
+  h->ycur = h->precision == COSENU_FP64 ? b->parity : 0;
   b->members.push_back(h);
   b->plan_ok = false;
   *member = h;
