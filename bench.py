@@ -469,7 +469,8 @@ def run_serving(args):
     second: all runs resident almost at once, so that leg's p50/p99 are close to its
     makespan).  On the same 70% arrivals, the runs served one at a time, each at its
     own precision (the same accuracy), and all in FP64 (the plain single-instance
-    path)."""
+    path); and the burst served one at a time at each run's own precision (the
+    throughput comparison under overload)."""
     from paper_2203_12866_gb300 import binding as b
     from paper_2203_12866_gb300 import inputs
 
@@ -490,6 +491,7 @@ def run_serving(args):
                                                  max_running=1)
         out["fp64_one_at_a_time_70pct"] = serve_trace(b, trace, budget, rate_scale=scale,
                                                       max_running=1, precision=b.COSENU_FP64)
+        out["one_at_a_time_burst"] = serve_trace(b, trace, budget, max_running=1)
     return out
 
 
