@@ -464,10 +464,10 @@ def serve_trace(b, trace, budget, rate_scale=1.0, max_running=0, precision=None)
 
 
 def run_serving(args):
-    """Continuous batching on the serving trace.  Leads with arrivals stretched to 70%
-    of the capacity the loop measures on the trace's own burst of arrivals (50 per
-    second: all runs resident almost at once, so that leg's p50/p99 are close to its
-    makespan).  On the same 70% arrivals, the runs served one at a time, each at its
+    """Continuous batching on the serving trace (at most --serve-max-running runs in the
+    batch at once).  Leads with arrivals stretched to 70% of the capacity the loop
+    measures on the trace's own burst of arrivals (50 per second: all runs queued
+    almost at once, a throughput figure).  On the same 70% arrivals, the runs served one at a time, each at its
     own precision (the same accuracy), and all in FP64 (the plain single-instance
     path); and the burst served one at a time at each run's own precision (the
     throughput comparison under overload)."""
@@ -477,14 +477,15 @@ def run_serving(args):
     trace = inputs.serving_trace(args.serve_requests, args.serve_rate,
                                  step_scale=args.serve_step_scale)
     budget = 64 << 30
-    burst = serve_trace(b, trace, budget)  # the capacity measurement
+    mr = args.serve_max_running
+    burst = serve_trace(b, trace, budget, max_running=mr)  # the capacity measurement
     cap = burst["completed_per_s"]
     scale = 0.7 * cap / args.serve_rate  # arrival times stretched to 70% of capacity
     out = {"workload": SERVE_WORKLOAD, "rate_per_s": args.serve_rate,
            "step_scale": args.serve_step_scale,
            "steps_range": [min(r["nsteps"] for r in trace), max(r["nsteps"] for r in trace)],
            "cell_updates": sum(2 * r["nz"] * r["nv"] * r["nsteps"] for r in trace)}
-    out["batched_70pct"] = serve_trace(b, trace, budget, rate_scale=scale)
+    out["batched_70pct"] = serve_trace(b, trace, budget, rate_scale=scale, max_running=mr)
     out["batched_burst"] = burst
     if args.serve_baselines:
         out["one_at_a_time_70pct"] = serve_trace(b, trace, budget, rate_scale=scale,
@@ -683,6 +684,8 @@ def main():
                     help="fraction of each run's t_final simulated (1 = the full trace)")
     ap.add_argument("--no-serve-baselines", dest="serve_baselines", action="store_false",
                     help="skip the one-at-a-time legs")
+    ap.add_argument("--serve-max-running", type=int, default=8,
+                    help="most runs batched at once in the continuous-batching legs (0: no limit)")
     ap.add_argument("--nz", type=int, default=NZ_FULL,
                     help="z cells (smaller values only for profiling captures)")
     args = ap.parse_args()
