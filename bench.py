@@ -81,6 +81,20 @@ def fp64_peak():
 FP64_PEAK_TFLOPS, FP64_PEAK_KIND = fp64_peak()
 
 
+def fp64_pipe_ops():
+    """FP64-pipe lane-operations per cell of each kernel of an FP64 step, counted by ncu
+    on the compiled kernels (profiles/fp64_pipe.json); None if absent or taken on
+    different source.  Every FP64 instruction occupies the pipe as long as an FMA, so
+    the pipe's limit is the FMA probe's rate in lane-operations: peak TFLOP/s / 2."""
+    path = os.path.join(ROOT, "profiles", "fp64_pipe.json")
+    if not os.path.exists(path):
+        return None
+    d = json.load(open(path))
+    if d.get("source_hash") != kernel_source_hash():
+        return None
+    return d["fp64_pipe_lane_ops_per_cell"]
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -268,6 +282,10 @@ def stage_roofline(stage_ms, stage_n, prec, scheme, hbm_peak):
             fl = FP64_FLOPS_PER_CELL[scheme][s] * 2 * NZ * NV
             rec["fp64_tflops"] = fl / (avg_ms * 1e-3) / 1e12
             rec["fp64_alu_frac"] = rec["fp64_tflops"] / FP64_PEAK_TFLOPS
+            ops = fp64_pipe_ops()
+            if ops is not None:  # pipe lane-operations per second against the FMA rate
+                rate = ops[scheme][s] * 2 * NZ * NV / (avg_ms * 1e-3)
+                rec["fp64_pipe_frac"] = rate / (FP64_PEAK_TFLOPS * 1e12 / 2)
         out.append(rec)
     return out
 
@@ -503,6 +521,8 @@ def summary(value, ms_step, roofline, variants, small, batched, serving):
            "dominant_frac": r3(roofline["frac"])}
     if variants:
         out["variants_ms_per_step"] = {k: r3(v["ms_per_step"]) for k, v in variants.items()}
+        out["fp64_pipe_frac"] = {k: r3(v["fp64_pipe_frac"]) for k, v in variants.items()
+                                 if "fp64_pipe_frac" in v}
     if small:
         out["small_us_per_step"] = {k: r3(v["us_per_step"]) for k, v in small.items()}
     if batched:
@@ -620,6 +640,10 @@ def run_ours(args, world, rank, local):
                     rec["bound"] = "alu"
                     rec["fp64_tflops"] = fl / (vms / k * 1e-3) / 1e12
                     rec["fp64_alu_frac"] = rec["fp64_tflops"] / FP64_PEAK_TFLOPS
+                    ops = fp64_pipe_ops()
+                    if ops is not None:  # the whole step against the FP64 pipe's rate
+                        rate = sum(ops[sc]) * cells / (vms / k * 1e-3)
+                        rec["fp64_pipe_frac"] = rate / (FP64_PEAK_TFLOPS * 1e12 / 2)
                     rec["fp64_peak_tflops"] = FP64_PEAK_TFLOPS
                     rec["fp64_peak_kind"] = FP64_PEAK_KIND
                 variants[f"{sc}_{pr}"] = rec
