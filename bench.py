@@ -66,6 +66,7 @@ KERNEL_NAMES = ("stage 1", "stage 2", "stage 3", "stage 4", "increment")
 FP64_FLOPS_PER_CELL = {"fdko": (81, 85, 85, 85, 32), "weno7": (531, 535, 535, 535, 32)}
 SCHEMES = {"fdko": 0, "weno7": 1}
 PRECS = {"fp64": 0, "mixed": 1}
+SMS = 152  # streaming multiprocessors of a GB300
 NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal (the measured copy bandwidth is the peak used)
 
 
@@ -81,18 +82,25 @@ def fp64_peak():
 FP64_PEAK_TFLOPS, FP64_PEAK_KIND = fp64_peak()
 
 
-def fp64_pipe_ops():
-    """FP64-pipe lane-operations per cell of each kernel of an FP64 step, counted by ncu
-    on the compiled kernels (profiles/fp64_pipe.json); None if absent or taken on
-    different source.  Every FP64 instruction occupies the pipe as long as an FMA, so
-    the pipe's limit is the FMA probe's rate in lane-operations: peak TFLOP/s / 2."""
-    path = os.path.join(ROOT, "profiles", "fp64_pipe.json")
+def kernel_counts(key):
+    """Per-cell instruction counts of the compiled kernels measured by ncu
+    (profiles/kernel_counts.json): "fp64_pipe_lane_ops_per_cell" (FP64-pipe lane
+    operations of each kernel of an FP64 step; every FP64 instruction occupies the pipe
+    as long as an FMA, so the pipe's limit is the FMA probe's rate in lane-operations,
+    peak TFLOP/s / 2) or "warp_inst_per_cell" (warp instructions of the mixed WENO7
+    stage kernels, against the issue limit of 4 per SM and clock).  None if absent or
+    taken on different source."""
+    path = os.path.join(ROOT, "profiles", "kernel_counts.json")
     if not os.path.exists(path):
         return None
     d = json.load(open(path))
     if d.get("source_hash") != kernel_source_hash():
         return None
-    return d["fp64_pipe_lane_ops_per_cell"]
+    return d.get(key)
+
+
+def fp64_pipe_ops():
+    return kernel_counts("fp64_pipe_lane_ops_per_cell")
 
 
 def peaks():
@@ -278,6 +286,11 @@ def stage_roofline(stage_ms, stage_n, prec, scheme, hbm_peak):
         gbs = byts / (avg_ms * 1e-3) / 1e9
         rec = {"kernel": KERNEL_NAMES[s], "stage": s + 1, "avg_ms": avg_ms, "alg_bytes": byts,
                "GB/s": gbs, "hbm_frac": gbs / hbm_peak, "total_ms": stage_ms[s]}
+        winst = kernel_counts("warp_inst_per_cell") if prec == "mixed" else None
+        if winst and f"{scheme}_{prec}" in winst and s < 4:
+            # warp instructions per second against 4 per SM and clock (2.07 GHz)
+            rate = winst[f"{scheme}_{prec}"][s] * 2 * NZ * NV / (avg_ms * 1e-3)
+            rec["issue_frac"] = rate / (4 * SMS * 2.07e9)
         if prec == "fp64":
             fl = FP64_FLOPS_PER_CELL[scheme][s] * 2 * NZ * NV
             rec["fp64_tflops"] = fl / (avg_ms * 1e-3) / 1e12
@@ -523,6 +536,9 @@ def summary(value, ms_step, roofline, variants, small, batched, serving):
         out["variants_ms_per_step"] = {k: r3(v["ms_per_step"]) for k, v in variants.items()}
         out["fp64_pipe_frac"] = {k: r3(v["fp64_pipe_frac"]) for k, v in variants.items()
                                  if "fp64_pipe_frac" in v}
+        out["issue_frac"] = {k: [r3(st["issue_frac"]) for st in v["stages"] if "issue_frac" in st]
+                             for k, v in variants.items()
+                             if any("issue_frac" in st for st in v["stages"])}
     if small:
         out["small_us_per_step"] = {k: r3(v["us_per_step"]) for k, v in small.items()}
     if batched:
