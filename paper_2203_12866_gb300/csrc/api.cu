@@ -148,12 +148,14 @@ namespace {
 
 // Per-stage launch traits of a (scheme, precision) pair.
 struct StageTraits {
-  int cols, header;
+  int cols, header, max_ring_rows;
+  int (*reducers)(int ncw);  // reducer warps for ncw consumer warps
 };
 
 template <int SCHEME, int PREC, int STAGE>
 StageTraits traits_of() {
-  return {stage_cols<SCHEME, PREC, STAGE>(), stage_smem_header_bytes<SCHEME, PREC, STAGE>()};
+  return {stage_cols<SCHEME, PREC, STAGE>(), stage_smem_header_bytes<SCHEME, PREC, STAGE>(),
+          stage_max_ring_rows<SCHEME, PREC>(), &stage_reducer_warps<SCHEME, PREC>};
 }
 
 template <int SCHEME, int PREC>
@@ -209,8 +211,9 @@ bool stage_args_complete(int precision, int stage, const StageArgs& a) {
 }
 
 int stage_block(int scheme, int precision, int nv, int stage) {
-  const int cols = stage_traits(scheme, precision, stage).cols;
-  return ((2 * nv + 32 * cols - 1) / (32 * cols)) * 32 + 64;
+  const StageTraits t = stage_traits(scheme, precision, stage);
+  const int ncw = (2 * nv + 32 * t.cols - 1) / (32 * t.cols);
+  return (ncw + 1 + t.reducers(ncw)) * 32;
 }
 
 // Ring shapes: R z rows per slot (one bulk copy per component plane moves R
@@ -222,14 +225,15 @@ std::vector<RingChoice> ring_choices(int scheme, int precision, int nv, int stag
                                      bool* query_failed) {
   std::vector<RingChoice> out;
   *query_failed = false;
-  const int header = stage_traits(scheme, precision, stage).header;
+  const StageTraits t = stage_traits(scheme, precision, stage);
+  const int header = t.header;
   const int block = stage_block(scheme, precision, nv, stage);
   for (int R = 1; R <= 32; R *= 2) {
     const int slot = slot_bytes_of(precision, nv, stage, R);
     for (int D = 2; D <= kMaxRing; ++D) {
-      // Consumer warps drift apart by at most D * R rows; the moment-slot
-      // barriers stay unambiguous only while that is <= kMomSlots - 2.
-      if (D * R > kMomSlots - 2) break;
+      // The warps of a CTA drift apart by at most D * R rows, which the moment
+      // slots bound (stage_max_ring_rows).
+      if (D * R > t.max_ring_rows) break;
       const size_t smem = (size_t)header + (size_t)D * slot;
       if (smem > (size_t)kStageSmemLimit) break;
       const int occ = max_blocks(scheme, precision, stage, batched, block, smem);

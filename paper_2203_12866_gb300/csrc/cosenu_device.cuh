@@ -22,12 +22,12 @@ constexpr uint32_t kErrTimeout = 2u;
 constexpr long long kWaitLimitCycles = 4000000000LL;
 
 // Ring of moment slots per CTA.  Consumer warps drift apart by at most
-// (ring depth) x (rows per slot) rows; the launch configuration keeps that at
-// most kMomSlots - 2 so that the per-row barriers of the ring stay unambiguous.
+// (ring depth) x (rows per slot) rows; the launch configuration keeps that
+// small enough for the per-row barriers of the ring to stay unambiguous
+// (stage_max_ring_rows).
 constexpr int kMomSlots = 16;
 constexpr int kMaxRing = 8;
 constexpr int kMaxWarps = 16;  // consumer warps: 2 * nv / 32 with nv <= 256
-constexpr int kMaxThreads = (kMaxWarps + 2) * 32;  // + producer and reducer warps
 
 // Arguments of one RK4 stage launch.  All arrays use the layout
 // [8 = species*4 + component][nz][nv]; Delta is double (FP64) or float (mixed).

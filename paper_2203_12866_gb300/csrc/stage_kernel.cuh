@@ -20,7 +20,9 @@
 //    ring of shared-memory slots up to `ring` rows ahead (full / empty
 //    mbarrier pairs);
 //  - a reducer warp: sums the consumers' per-warp partial velocity moments of
-//    each row and publishes the row's moments through an mbarrier.
+//    each row and publishes the row's moments through an mbarrier (mixed
+//    WENO7: up to four reducer warps, taking rows in turn, sum the moments
+//    from the ring slots themselves).
 // Consumer warps never meet at a CTA-wide barrier: a row's moments are
 // produced while the row waits `lag` iterations to become the center, so the
 // mbarrier waits are normally already satisfied.  Because the CTA holds every
@@ -99,6 +101,52 @@ __host__ __device__ constexpr int stage_max_consumer_warps() {
   return kMaxWarps / stage_cols<SCHEME, PREC, STAGE>();
 }
 
+// Who sums a row's velocity moments.  In the mixed WENO7 kernels the consumer
+// warps are bound by instruction issue, so the reducer warps sum the moments of
+// delta_{s-1} themselves, straight from the ring slot (one pass over the row,
+// one warp reduction), instead of every consumer warp summing its columns and
+// reducing them across its lanes.  Elsewhere the consumers publish per-warp
+// partials and one reducer warp adds them.
+template <int SCHEME, int PREC>
+__host__ __device__ constexpr bool stage_reducer_moments() {
+  return SCHEME == kWENO7 && PREC == kMIXED;
+}
+
+// Reducer warps of a kernel with ncw consumer warps.  With the moments summed
+// by the reducers and 16 consumer warps (nv = 256), rows are dealt round-robin
+// to three of them, so that the producer and the reducers sit one on each of
+// the SM's four schedulers (warp w runs on scheduler w mod 4) and no scheduler
+// holds more than five warps (a sixth would cap the registers at 80).  Smaller
+// CTAs keep one reducer: two of them then stay resident per SM at 96 registers
+// (measured, 256-grid batched step: nv = 128 WENO7 stages 2.45 ms with one
+// reducer and two CTAs per SM, 2.69 ms with three reducers and one CTA).
+template <int SCHEME, int PREC>
+__host__ __device__ constexpr int stage_reducer_warps(int ncw) {
+  return !stage_reducer_moments<SCHEME, PREC>() ? 1 : ncw >= 16 ? 3 : 1;
+}
+
+// Moment slots (per-row barriers and moments) of a kernel's ring.  The kernels
+// whose reducers read the ring keep 32, which leaves room for rings of up to 26
+// rows (stage_max_ring_rows).
+template <int SCHEME, int PREC>
+__host__ __device__ constexpr int stage_mom_slots() {
+  return stage_reducer_moments<SCHEME, PREC>() ? 2 * kMomSlots : kMomSlots;
+}
+
+// Most rows the bulk-copy ring may hold (ring depth x rows per slot).  Consumer
+// warps drift apart by at most that many rows, and the moment-slot barriers stay
+// unambiguous while the drift is at most (slots - 2).  Reducers that read the
+// slots run up to that many rows ahead of the slowest consumer, and may reuse a
+// row's moment slot only after every consumer has finished that row as a center
+// (it enters lag rows after it, with up to two rows read per iteration): at most
+// (slots - lag - 2).
+template <int SCHEME, int PREC>
+__host__ __device__ constexpr int stage_max_ring_rows() {
+  return stage_reducer_moments<SCHEME, PREC>()
+             ? stage_mom_slots<SCHEME, PREC>() - Scheme<SCHEME>::kLag - 2
+             : stage_mom_slots<SCHEME, PREC>() - 2;
+}
+
 template <typename T, int N>
 __device__ __forceinline__ void vload(const T* p, T (&out)[N]) {
   if constexpr (N == 1) {
@@ -151,23 +199,32 @@ __host__ __device__ inline SlotLayout slot_layout(int nv, int stage, int R) {
   return L;
 }
 
-// Shared memory besides the ring.  Acc is the type of the moment partials.
-//   mbarriers: full[kMaxRing] empty[kMaxRing] part[kMomSlots] mom[kMomSlots]
-//   flags (abort), partials [kMomSlots][NW consumer warps][8] Acc, finished
-//   moments or the Hamiltonian's coefficients [kMomSlots][2 species][8] Acc,
-//   running moments of y (mixed) [kMomSlots][8] double.
-template <int PREC, int NW>
+// Shared memory besides the ring, for MS moment slots.  Acc is the type of the
+// moment partials.
+//   mbarriers: full[kMaxRing] empty[kMaxRing] part[MS] mom[MS]
+//   flags (abort), partials [MS][NWP warps][8] Acc (NWP = 0 where the reducers
+//   sum the moments), finished moments or the Hamiltonian's coefficients
+//   [MS][2 species][8] Acc, running moments of y (mixed) [MS][8] double.
+template <int PREC, int NWP, int MS>
 struct SmemHeader {
   using Acc = typename Prec<PREC>::Real;
   static constexpr int kBars = 0;
-  static constexpr int kNumBars = 2 * kMaxRing + 2 * kMomSlots;
+  static constexpr int kNumBars = 2 * kMaxRing + 2 * MS;
   static constexpr int kFlags = kBars + kNumBars * 8;
   static constexpr int kPart = ((kFlags + 64) + 127) & ~127;
-  static constexpr int kPartBytes = kMomSlots * NW * 8 * (int)sizeof(Acc);
+  static constexpr int kPartBytes = MS * NWP * 8 * (int)sizeof(Acc);
   static constexpr int kMomf = kPart + kPartBytes;
-  static constexpr int kMyRing = kMomf + kMomSlots * 16 * (int)sizeof(Acc);
-  static constexpr int kBytes = ((kMyRing + kMomSlots * 8 * 8) + 127) & ~127;
+  static constexpr int kMyRing = kMomf + MS * 16 * (int)sizeof(Acc);
+  static constexpr int kBytes = ((kMyRing + MS * 8 * 8) + 127) & ~127;
 };
+
+// The header type of one stage kernel.
+template <int SCHEME, int PREC, int STAGE>
+using StageHeader =
+    SmemHeader<PREC,
+               stage_reducer_moments<SCHEME, PREC>() ? 0
+                                                     : stage_max_consumer_warps<SCHEME, PREC, STAGE>(),
+               stage_mom_slots<SCHEME, PREC>()>;
 
 // Calls f(std::integral_constant<int, K>) for K = B .. E-1 (compile-time unrolled).
 template <int B, int E, typename F>
@@ -342,10 +399,11 @@ __device__ __forceinline__ void weno7_face_pair(float x0, float x1, float x2, fl
 // ---------------------------------------------------------------- the kernel
 
 // Largest CTA of a stage kernel: consumer warps for 256 v-columns per species,
-// plus the producer and reducer warps.
+// plus the producer and the reducer warps.
 template <int SCHEME, int PREC, int STAGE>
 __host__ __device__ constexpr int stage_max_threads() {
-  return (stage_max_consumer_warps<SCHEME, PREC, STAGE>() + 2) * 32;
+  constexpr int nw = stage_max_consumer_warps<SCHEME, PREC, STAGE>();
+  return (nw + 1 + stage_reducer_warps<SCHEME, PREC>(nw)) * 32;
 }
 
 // Minimum resident CTAs per SM the compiler is told to allow for.  The mixed
@@ -364,7 +422,7 @@ __host__ __device__ constexpr int stage_min_blocks() {
 // Shared memory of a stage kernel besides its ring slots.
 template <int SCHEME, int PREC, int STAGE>
 __host__ __device__ constexpr int stage_smem_header_bytes() {
-  return SmemHeader<PREC, stage_max_consumer_warps<SCHEME, PREC, STAGE>()>::kBytes;
+  return StageHeader<SCHEME, PREC, STAGE>::kBytes;
 }
 
 
