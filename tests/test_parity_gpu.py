@@ -74,6 +74,26 @@ def test_mixed_ragged_tiles(scheme, nz, nv):
     assert rel_by_component(got, ref) <= MIXED_REL_TOL
 
 
+@pytest.mark.parametrize("scheme", ["fdko", "weno7"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("nz,nv", [(600, 252), (911, 132), (1000, 256)])
+def test_wide_rows(scheme, prec, nz, nv):
+    """Long v-rows with several rows per CTA: nv = 252 and 256 give the mixed
+    WENO7 kernel 16 consumer warps and three reducer warps taking the rows in
+    turn (nv = 252 and 132 leave the reducers' second column chunk partly
+    empty); nv = 252 and 132 put both species in one warp (the consumers apply
+    the moments' species sign), nv = 256 one species per warp (the reducer
+    applies it per warp)."""
+    u0 = inputs.random_state(nz, nv, seed=nz + nv, offdiag=0.05)
+    kw = dict(mu=0.7, omega=0.2, theta=0.3)
+    got = run_gpu(u0, 0.2 * nz, SCHEMES[scheme], PRECS[prec], 6, **kw)
+    ref = run_oracle(u0, 0.2 * nz, SCHEMES[scheme], 6, **kw)
+    if prec == "fp64":
+        assert max_abs(got, ref) <= FP64_TOL
+    else:
+        assert rel_by_component(got, ref) <= MIXED_REL_TOL
+
+
 @pytest.mark.parametrize("scheme", ["fdko", "weno7", "fdko3"])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("nz", [1, 2, 3, 5, 9])
