@@ -77,6 +77,9 @@ void count_launches(int n);                     // cosenu_kernel_launches counte
 // columns (2 columns per thread for FD4+KO, 1 for WENO7), a producer and a reducer warp.
 int stage_block(int scheme, int precision, int nv, int stage);
 
+// Halo rows a CTA's march reads besides its own z range (below and above).
+int stage_halo_rows(int scheme);
+
 // Admissible ring shapes of one stage kernel, best first: the largest copy
 // size per plane times resident CTAs (capped at 4 KB), then the most resident
 // CTAs, then the deepest ring.  Empty if none fits; *query_failed is set if an
