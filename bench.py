@@ -57,13 +57,14 @@ STAGE_BYTES = {"fp64": (16, 24, 24, 24, 48), "mixed": (8, 12, 12, 12, 36)}
 KERNEL_NAMES = ("stage 1", "stage 2", "stage 3", "stage 4", "increment")
 # FP64 flops per cell (4 reals) per launch of the fp64 kernels, counted from the
 # kernels' arithmetic (FMA = 2 flops, a reciprocal = 1): stage input y + delta 4
-# (stages 2-4), v-moment partials with the warp reduction 20 (FD4+KO, two
-# columns per thread) or 26 (WENO7, one), Hamiltonian 6 (one FMA per component
-# from the reducer's coefficients), commutator 11, advection 40 (FD4+KO: one
-# FMA per window row, the two stencils combined) or 484 (WENO7: 117 per face
-# for the reconstruction in differences, 4 for the flux difference), output 4
-# (delta_s); the increment kernel 32 (four FMA per real).
-FP64_FLOPS_PER_CELL = {"fdko": (81, 85, 85, 85, 32), "weno7": (531, 535, 535, 535, 32)}
+# (stages 2-4), v-moment partials with the warp reduction 18 (FD4+KO, two
+# columns per thread) or 22 (WENO7, one; the species sign is the reducer's),
+# Hamiltonian 6 (one FMA per component from the reducer's coefficients, which
+# carry the stage factor), commutator 11, advection 40 (FD4+KO: one FMA per
+# window row, the two stencils combined, the stage factor in the weights) or
+# 480 (WENO7: 117 per face for the reconstruction in differences, 3 for the
+# flux difference); the increment kernel 32 (four FMA per real).
+FP64_FLOPS_PER_CELL = {"fdko": (75, 79, 79, 79, 32), "weno7": (519, 523, 523, 523, 32)}
 SCHEMES = {"fdko": 0, "weno7": 1}
 PRECS = {"fp64": 0, "mixed": 1}
 SMS = 152  # streaming multiprocessors of a GB300
