@@ -344,6 +344,10 @@ ApplySeg apply_seg(const cosenu_s* h) {
   sg.rows_per_chunk = apply_rows_per_chunk(h->nv);
   sg.nchunks = (8 * h->nz + sg.rows_per_chunk - 1) / sg.rows_per_chunk;
   sg.err = h->err;
+  // the mixed WENO7 stages store their increments times kWenoScale
+  const double inv = h->scheme == COSENU_WENO7 ? kWenoInvScale : 1.0;
+  sg.w3 = (float)(inv / 3.0);
+  sg.w6 = (float)(inv / 6.0);
   return sg;
 }
 

@@ -49,8 +49,8 @@ struct StageArgs {
   double weno_eps;
   const double* y_in;     // fp64: state at the start of the step (read with halo)
   const float* y32_in;    // mixed: float copy of the state (read with halo)
-  const void* d_in;       // stage s > 1: delta_{s-1} (read with halo)
-  void* d_out;            // delta_s
+  const void* d_in;       // stage s > 1: delta_{s-1} (read with halo; mixed WENO7: times kWenoScale)
+  void* d_out;            // delta_s (mixed WENO7: times kWenoScale)
   double* my;             // mixed: running FP64 moments of y, [nz][8] (6 used)
   const double* vtab;     // beam velocities v_j [nv], then quadrature weights w_j [nv]
   uint32_t* err;          // device error flags

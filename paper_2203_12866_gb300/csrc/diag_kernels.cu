@@ -97,12 +97,13 @@ __global__ void y32_moments_kernel(const double* __restrict__ y, float* __restri
 }
 
 // The step's float increment of four reals from the stage increments,
-// (delta_1 + 2 delta_2 + delta_3) / 3 + delta_4 / 6 (classic RK4 with
-// delta_1,2 = dt/2 k_1,2 and delta_3,4 = dt k_3,4); then y[0..3] += it in
+// (delta_1 + 2 delta_2 + delta_3) t + delta_4 s with t = 1/3, s = 1/6 (classic
+// RK4 with delta_1,2 = dt/2 k_1,2 and delta_3,4 = dt k_3,4; t and s also divide
+// out the scale of increments stored scaled); then y[0..3] += it in
 // double and the float copy of the four results.  Returns false if a result is
 // not finite.
-__device__ __forceinline__ float4 rk4_increment(float4 a, float4 b, float4 c, float4 d) {
-  const float t = 1.0f / 3.0f, s = 1.0f / 6.0f;
+__device__ __forceinline__ float4 rk4_increment(float4 a, float4 b, float4 c, float4 d, float t,
+                                                float s) {
   return make_float4((a.x + 2.0f * b.x + c.x) * t + d.x * s, (a.y + 2.0f * b.y + c.y) * t + d.y * s,
                      (a.z + 2.0f * b.z + c.z) * t + d.z * s, (a.w + 2.0f * b.w + c.w) * t + d.w * s);
 }
@@ -206,8 +207,8 @@ __device__ __forceinline__ void apply_chunk(const ApplySeg& sg, int64_t ch, floa
       const float2 m0 = dot4_ff(w, wl, inc), m1 = dot4_ff(wv, wvl, inc);
       sm[gg] = make_float4(m0.x, m0.y, m1.x, m1.y);
     };
-    one(g, ia, rk4_increment(a1, a2, a3, a4));
-    if (two) one(gb, ib, rk4_increment(b1, b2, b3, b4));
+    one(g, ia, rk4_increment(a1, a2, a3, a4, sg.w3, sg.w6));
+    if (two) one(gb, ib, rk4_increment(b1, b2, b3, b4, sg.w3, sg.w6));
   }
   if (__ballot_sync(0xffffffffu, bad) && (tid & 31) == 0) atomicOr(sg.err, kErrNonFinite);
   __syncthreads();

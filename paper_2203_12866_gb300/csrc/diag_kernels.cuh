@@ -32,6 +32,8 @@ struct ApplySeg {
   int32_t rows_per_chunk;
   int64_t nchunks;      // ceil(8 nz / rows_per_chunk)
   uint32_t* err;
+  float w3, w6;         // dy = (delta_1 + 2 delta_2 + delta_3) w3 + delta_4 w6: 1/3 and 1/6
+                        // divided by the scale the stages store their increments in
 };
 
 // One FP64 state for the FP64 increment kernel: n2 = 4 nz nv double2 groups.

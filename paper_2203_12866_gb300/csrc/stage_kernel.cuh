@@ -331,18 +331,28 @@ __device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, 
 __device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
+// The float faces take the cell values scaled by kWenoScale = sqrt(781/3) and
+// return the face value scaled by the same factor: the third-difference term
+// (781/3) c^2 of the smoothness indicators is then the square of the scaled
+// difference, without a multiply, and the other terms take their coefficients
+// divided by the scale.  The mixed WENO7 kernels keep their stage increments in
+// that scale (the reconstruction and the right-hand side are linear in it).
+constexpr float kWenoScale = 16.13484841370793f;
+constexpr double kWenoInvScale = 0.06197765075688065;  // 1 / sqrt(781/3)
+
 // float: fast reciprocals for the weights (the mixed path's weights need no more).
-// The face from its differences e_-3..e_2, g_-3..g_1 and the third-difference
-// terms T_r = (781/3) c_r^2 + eps (T_0 from h_0 .. T_3 from h_-3).  Every
-// operation is an explicit rounding (see mul_rn), so two faces evaluated in one
-// pass from shared differences are each bitwise what a lone evaluation gives.
+// The face from its scaled differences e_-3..e_2, g_-3..g_1 and the
+// third-difference terms T_r = (781/3) c_r^2 + eps = (kWenoScale c_r)^2 + eps
+// (T_0 from h_0 .. T_3 from h_-3).  Every operation is an explicit rounding (see
+// mul_rn), so two faces evaluated in one pass from shared differences are each
+// bitwise what a lone evaluation gives.
 __device__ __forceinline__ float weno7_face_core(float f0, float em3, float em2, float em1,
                                                  float e0, float e1, float e2, float gm3,
                                                  float gm2, float gm1, float g0, float g1,
                                                  float T0, float T1, float T2, float T3) {
-  constexpr float s1 = 2.5819888974716112f;  // sqrt(20/3)
-  constexpr float s2 = 16.124515496597099f;  // sqrt(260)
-  // sqrt(20/3) a_r and sqrt(260) b_r
+  constexpr float s1 = 0.16002560614563885f;  // sqrt(20/3) / kWenoScale
+  constexpr float s2 = 0.9993595900720049f;   // sqrt(260) / kWenoScale
+  // sqrt(20/3) a_r and sqrt(260) b_r (unscaled: the differences carry kWenoScale)
   const float a0 = fma_rn(2.0f * s1, e2, fma_rn(-7.0f * s1, e1, mul_rn(11.0f * s1, e0)));
   const float a1 = fma_rn(-s1, e1, fma_rn(5.0f * s1, e0, mul_rn(2.0f * s1, em1)));
   const float a2 = fma_rn(2.0f * s1, e0, fma_rn(5.0f * s1, em1, mul_rn(-s1, em2)));
@@ -355,8 +365,8 @@ __device__ __forceinline__ float weno7_face_core(float f0, float em3, float em2,
   const float t1 = fma_rn(a1, a1, fma_rn(b12, b12, T1));
   const float t2 = fma_rn(a2, a2, fma_rn(b12, b12, T2));
   const float t3 = fma_rn(a3, a3, fma_rn(b3, b3, T3));
-  // d_r delta_r: the linear weights 4/35, 18/35, 12/35, 1/35 folded into the
-  // candidates' coefficients
+  // d_r delta_r (scaled like the values): the linear weights 4/35, 18/35,
+  // 12/35, 1/35 folded into the candidates' coefficients
   const float dd0 = fma_rn(1.0f / 105.0f, e2, fma_rn(-4.0f / 105.0f, e1, mul_rn(3.0f / 35.0f, e0)));
   const float dd1 = fma_rn(-3.0f / 70.0f, e1, fma_rn(9.0f / 35.0f, e0, mul_rn(3.0f / 70.0f, em1)));
   const float dd2 = fma_rn(3.0f / 35.0f, e0, fma_rn(4.0f / 35.0f, em1, mul_rn(-1.0f / 35.0f, em2)));
@@ -372,24 +382,22 @@ __device__ __forceinline__ float weno7_face_core(float f0, float em3, float em2,
   return add_rn(f0, mul_rn(num, rcp_approx(ws)));
 }
 
-// Two adjacent float faces from eight values x_0..x_7: P from x_0..x_6 (f_0 =
-// x_3) and Q from x_1..x_7 (f_0 = x_4).  The differences and the third-difference
-// terms of the overlapping stencils are formed once (each is the same rounded
-// value whichever face uses it), so P and Q are bitwise the faces a lone
-// evaluation of their seven values gives.
+// Two adjacent float faces from eight scaled values x_0..x_7: P from x_0..x_6
+// (f_0 = x_3) and Q from x_1..x_7 (f_0 = x_4), both scaled by kWenoScale.  The
+// differences and the third-difference terms of the overlapping stencils are
+// formed once (each is the same rounded value whichever face uses it), so P and
+// Q are bitwise the faces a lone evaluation of their seven values gives.
 __device__ __forceinline__ void weno7_face_pair(float x0, float x1, float x2, float x3, float x4,
                                                 float x5, float x6, float x7, float eps,
                                                 float& P, float& Q) {
-  constexpr float c3 = 781.0f / 3.0f;
   const float e0 = sub_rn(x1, x0), e1 = sub_rn(x2, x1), e2 = sub_rn(x3, x2), e3 = sub_rn(x4, x3),
               e4 = sub_rn(x5, x4), e5 = sub_rn(x6, x5), e6 = sub_rn(x7, x6);
   const float g0 = sub_rn(e1, e0), g1 = sub_rn(e2, e1), g2 = sub_rn(e3, e2), g3 = sub_rn(e4, e3),
               g4 = sub_rn(e5, e4), g5 = sub_rn(e6, e5);
   const float h0 = sub_rn(g1, g0), h1 = sub_rn(g2, g1), h2 = sub_rn(g3, g2), h3 = sub_rn(g4, g3),
               h4 = sub_rn(g5, g4);
-  const float T0 = fma_rn(mul_rn(c3, h0), h0, eps), T1 = fma_rn(mul_rn(c3, h1), h1, eps),
-              T2 = fma_rn(mul_rn(c3, h2), h2, eps), T3 = fma_rn(mul_rn(c3, h3), h3, eps),
-              T4 = fma_rn(mul_rn(c3, h4), h4, eps);
+  const float T0 = fma_rn(h0, h0, eps), T1 = fma_rn(h1, h1, eps), T2 = fma_rn(h2, h2, eps),
+              T3 = fma_rn(h3, h3, eps), T4 = fma_rn(h4, h4, eps);
   // local indices: e_-3 .. e_2 = e[b] .. e[b+5], g_-3 .. g_1 = g[b] .. g[b+4],
   // h_-3 .. h_0 = h[b] .. h[b+3] for the stencil starting at x_b
   P = weno7_face_core(x3, e0, e1, e2, e3, e4, e5, g0, g1, g2, g3, g4, T3, T2, T1, T0);
