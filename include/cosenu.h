@@ -444,11 +444,11 @@ const char* cosenu_server_last_error(cosenu_server_t s);
  * The work is enqueued on `stream` (a cudaStream_t; NULL = legacy default
  * stream) and the call returns without waiting.
  *
- * Who needs it: code that must not call cudaMalloc -- for example a caller that
- * records its work into a CUDA graph with stream capture (allocation is not
- * allowed while capturing), or a process whose device memory is already fully
- * handed to another allocator (a framework's caching pool, a serving budget) --
- * and code that cannot afford the synchronisation an allocation may imply.
+ * Who needs it: callers that cannot call cudaMalloc -- a process whose device
+ * memory is already fully handed to another allocator (a framework's caching
+ * pool, a serving loop's fixed budget), where one more cudaMalloc would fail or
+ * break the budget, and code on a latency-critical path that cannot afford the
+ * device-wide synchronisation that cudaFree implies.
  * This function calls no cudaMalloc, cudaFree or other allocating routine.
  *
  * Scratch: the per-block partial sums live in one static device array of the

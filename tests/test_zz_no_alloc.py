@@ -1,8 +1,8 @@
 """The allocation-free diagnostics entry point, cosenu_conserved_noalloc.
 
-It serves callers that may not call cudaMalloc (stream capture, memory already
-handed to another allocator): its scratch is a static device array of the
-library.  The test calls it through the C ABI on a state held by a solver and
+It serves callers that cannot call cudaMalloc (device memory already handed to
+another allocator or held to a fixed budget): its scratch is a static device
+array of the library.  The test calls it through the C ABI on a state held by a solver and
 compares its eight outputs with those of cosenu_conserved, the allocating entry
 point, on two calls in a row (the second after more steps, so stale scratch
 would show).  It also checks the rejection of grids larger than the scratch.
