@@ -367,7 +367,7 @@ cudaError_t launch_kernel(cosenu_batch_t b, int ci, int k, int par, cudaStream_t
   if (k == 5) {
     const ApplySeg* segs = reinterpret_cast<const ApplySeg*>(b->tables + c.seg_off);
     const int64_t* cf = reinterpret_cast<const int64_t*>(b->tables + c.chunk_off);
-    const int64_t blocks = std::min<int64_t>(c.nchunks, (int64_t)b->nsm * 8);
+    const int64_t blocks = std::min<int64_t>(c.nchunks, (int64_t)b->nsm * 6);  // two waves of three per SM
     apply_increment_batch_kernel<<<(int)blocks, kApplyThreads, 0, st>>>(segs, cf, c.nseg,
                                                                         c.nchunks);
     return cudaGetLastError();

@@ -245,18 +245,23 @@ __global__ void __launch_bounds__(kApplyThreads, 4) apply_increment_kernel(Apply
 }
 
 // The same for several states: chunks chunk_first[k] .. chunk_first[k + 1] - 1
-// of the launch belong to segment k; blocks walk the chunks.  Non-finite
-// results are reported in the segment's own error word.
-__global__ void __launch_bounds__(kApplyThreads, 4) apply_increment_batch_kernel(
+// of the launch belong to segment k; blocks walk the chunks in increasing order,
+// so each search starts from the previous chunk's segment.  Non-finite results
+// are reported in the segment's own error word.  Three blocks per SM: the
+// segment's fields come from memory here (the single-grid kernel has them in its
+// parameters), and at four blocks' 64 registers they spilled.
+__global__ void __launch_bounds__(kApplyThreads, 3) apply_increment_batch_kernel(
     const ApplySeg* __restrict__ segs, const int64_t* __restrict__ chunk_first, int nseg,
     int64_t nchunks) {
   __shared__ float4 sm[kApplyGroups];
+  int seg = 0;
   for (int64_t ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
-    int lo = 0, hi = nseg - 1;  // last segment whose first chunk is <= ch
+    int lo = seg, hi = nseg - 1;  // last segment whose first chunk is <= ch
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
       if (chunk_first[mid] <= ch) lo = mid; else hi = mid - 1;
     }
+    seg = lo;
     apply_chunk(segs[lo], ch - chunk_first[lo], sm);
   }
 }

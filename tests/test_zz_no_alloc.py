@@ -5,7 +5,8 @@ another allocator or held to a fixed budget): its scratch is a static device
 array of the library.  The test calls it through the C ABI on a state held by a solver and
 compares its eight outputs with those of cosenu_conserved, the allocating entry
 point, on two calls in a row (the second after more steps, so stale scratch
-would show).  It also checks the rejection of grids larger than the scratch.
+would show), and that the second call leaves the device's free memory unchanged.  It also
+checks the rejection of grids larger than the scratch.
 The file is collected last; it needs nothing from the other tests.
 """
 import numpy as np
@@ -37,8 +38,11 @@ def test_conserved_noalloc_matches_allocating_entry_point():
                       ref["dP_mean"]]
             y_dev = binding.cosenu_state_device(s.h)
             torch.cuda.synchronize()
+            free_before = torch.cuda.mem_get_info()[0]
             binding.cosenu_conserved_noalloc(y_dev, nz, nv, L, theta, out.data_ptr(), 0)
             torch.cuda.synchronize()
+            if call == 1:  # the first call may load the library's device code; later ones take nothing
+                assert torch.cuda.mem_get_info()[0] == free_before
             got = out.cpu().numpy()
             assert np.allclose(got, expect, rtol=1e-12, atol=1e-15), (call, got, expect)
 
