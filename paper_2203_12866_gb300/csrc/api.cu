@@ -29,11 +29,17 @@ thread_local std::string tl_error;
 
 constexpr size_t kAlign = 256;
 // Fewest z rows per CTA of a single-grid launch.  A CTA's march is latency-bound
-// per row, so a small grid is spread over as many SMs as it can use: at 4 rows
-// (plus the 2 lag halo rows each side) the 512 x 32 FP64 FD4+KO step takes 114 us
-// against 320 us at 16 rows; grids of more than SMs x resident CTAs x 4 rows
+// per row (and an FP64 CTA of few columns waits on one scheduler's share of the
+// FP64 pipe), so a small grid is spread over as many SMs and schedulers as it
+// can use.  Measured on the 512 x 32 steps (us per step for 4 / 2 / 1 rows):
+// FD4+KO FP64 109 / 66 / 55, FD4+KO mixed 63 / 49 / 54, WENO7 FP64 306 / 222 / 249,
+// WENO7 mixed 69 / 78 / 84 (its march takes two rows per iteration); 16 rows gave
+// 320 us for FD4+KO FP64.  Grids of more than SMs x resident CTAs x this many rows
 // are unaffected.
-constexpr int64_t kMinRowsPerCta = 4;
+int64_t min_rows_per_cta(int scheme, int precision) {
+  if (scheme == COSENU_WENO7) return precision == COSENU_FP64 ? 2 : 4;
+  return precision == COSENU_FP64 ? 1 : 2;  // FD4+KO, r = 2 and 3
+}
 
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
@@ -110,7 +116,7 @@ cudaError_t launch_stage(cosenu_t h, int stage, const StageArgs& a) {
 
 // Launch shape of each stage: the best ring shape of ring_choices() and a
 // persistent grid of at most SMs x resident CTAs, contiguous z ranges of at
-// least kMinRowsPerCta rows.  A shape whose slot holds more than half of the
+// least min_rows_per_cta() rows.  A shape whose slot holds more than half of the
 // rows a CTA marches (its z range and halo) is passed over while a smaller one
 // fits: on short grids the march would otherwise wait for one large first copy
 // (512 x 32 mixed WENO7 steps: 8-row slots 102 us, 4-row slots 72 us).
@@ -134,7 +140,8 @@ int configure(cosenu_t h) {
       c.slot_bytes = ch.slot_bytes;
       c.smem = ch.smem;
       const int64_t max_grid = (int64_t)nsm * ch.occ;
-      int64_t grid = (h->nz + kMinRowsPerCta - 1) / kMinRowsPerCta;
+      const int64_t min_rows = min_rows_per_cta(h->scheme, h->precision);
+      int64_t grid = (h->nz + min_rows - 1) / min_rows;
       if (grid > max_grid) grid = max_grid;
       if (grid < 1) grid = 1;
       c.rows = (h->nz + grid - 1) / grid;
